@@ -1,0 +1,21 @@
+"""Shared pytest configuration: the ``gpu`` marker and the repository root on sys.path."""
+
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
+    config.addinivalue_line("markers", "slow: longer CPU oracle runs")
+
+
+@pytest.fixture(scope="session")
+def cloud5k():
+    from paper_2108_07031_gb300 import cloud
+    return cloud.naca0012_cloud(128, 40)
