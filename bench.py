@@ -1,0 +1,379 @@
+"""Benchmark of the q-LSKUM hot path on GB300: point-iterations per second.
+
+One step = one pseudo-time iteration of Algorithm 1 over the whole cloud: the
+local time step, four SSP-RK stages of {q-variables, q-derivatives with two
+inner iterations, flux residual, state update} and the residue. Workload: the
+synthetic NACA 0012 O-cloud with 10M points (5658 x 1768, shuffled input
+order), M = 0.63, alpha = 2 deg, FP64. Inputs (the 12 GB device working set)
+are far larger than L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (oracle/) on the host cores instead, on
+a bounded sample of the same workload. With N > 1 (torchrun) every rank runs
+an independent replica on its own GPU (the solver has no data-path exchange
+on one cloud per GPU); the reference arm runs on rank 0 only.
+
+Prints one JSON line on rank 0.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "q-LSKUM point-iterations/s (FP64 vs mixed vs batched), % of HBM roofline"
+UNIT = "point-iterations/s"
+WORKLOAD_POINTS = 10_000_000
+MACH, ALPHA = 0.63, 2.0
+SAMPLE_POINTS = 2_500_000  # CPU-oracle sample of the same cloud family
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def _cloud(n_points: int, shuffle: bool = True):
+    from paper_2108_07031_gb300 import cloud as Cl
+    n_c, n_r = Cl.cloud_dims(n_points)
+    cache = os.environ.get("LSKUM_CLOUD_CACHE", os.path.join(tempfile.gettempdir(), "lskum_clouds"))
+    fn = os.path.join(cache, f"naca_{n_c}x{n_r}_s{int(shuffle)}.npz")
+    if os.path.exists(fn):
+        try:
+            z = np.load(fn)
+            return Cl.Cloud(xy=z["xy"], normals=z["normals"], flags=z["flags"],
+                            nbr_offsets=z["off"], nbr_idx=z["idx"], n_c=n_c, n_r=n_r,
+                            k=z["k"], l=z["l"])
+        except Exception:
+            pass
+    c = Cl.naca0012_cloud(n_c, n_r, shuffle=shuffle)
+    try:
+        os.makedirs(cache, exist_ok=True)
+        tmp = fn + f".{os.getpid()}.npz"
+        np.savez(tmp, xy=c.xy, normals=c.normals, flags=c.flags, off=c.nbr_offsets,
+                 idx=c.nbr_idx, k=c.k, l=c.l)
+        os.replace(tmp, fn)
+    except OSError:
+        pass
+    return c
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.out = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.out, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        try:
+            self.out.flush()
+            with open(self.out.name) as f:
+                rows = [r.strip().split(", ") for r in f if r.strip()]
+        except OSError:
+            rows = []
+        finally:
+            try:
+                os.unlink(self.out.name)
+            except OSError:
+                pass
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if r[5 + k].strip().lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _fp64_peak():
+    """FP64 pipe throughput and FP64 library-call costs measured live by the probe."""
+    from paper_2108_07031_gb300 import build as B
+    try:
+        out = subprocess.run([B.PROBE], capture_output=True, text=True, timeout=120, check=True)
+        return json.loads(out.stdout.strip().splitlines()[-1])
+    except Exception as e:  # the probe is a measurement aid; report without it
+        return {"error": str(e)}
+
+
+def fp64_work_per_launch(cloud, peaks):
+    """Algorithmic FP64 work of one flux/update launch, in flop-equivalents.
+
+    Explicit flops of the method's formulas (an add, multiply or compare-free
+    select is 1, a fused multiply-add 2) per neighbour and per point, plus
+    each transcendental or division weighted by its measured FP64-pipe cost on
+    this GPU (flop-equivalents = FP64 peak / calls per second):
+      per neighbour: q~_j and q~_0 (32), two q~ -> W maps (24 + 2 log, 2 exp,
+        2 sqrt, 2 div), accumulation (12 per split stencil)
+      per split-flux evaluation (two per split stencil a neighbour is in):
+        30 + erfc + exp + div
+      per point: stage update, wall condition and next q-variables
+        (40 + 2 log + 2 div)
+    """
+    calls = peaks.get("fp64_calls_gcalls_per_s", {})
+    peak = peaks.get("fp64_fma_tflops", 1.25) * 1e12
+    cost = {k: peak / (calls[k] * 1e9) if calls.get(k) else d
+            for k, d in (("erfc", 120.0), ("exp", 34.0), ("log", 62.0), ("sqrt", 19.0), ("rcp", 13.0))}
+    off = cloud.nbr_offsets.astype(np.int64)
+    deg = np.diff(off)
+    # every neighbour is in one s-stencil and one n-stencil except boundary
+    # exclusions and exact ties; at interior points both apply
+    nbr = int(deg.sum())
+    stencils = 2 * nbr
+    per_nbr = 32 + 24 + 2 * (cost["log"] + cost["exp"] + cost["sqrt"] + cost["rcp"])
+    per_flux_eval = 30 + cost["erfc"] + cost["exp"] + cost["rcp"]
+    per_stencil = 12 + 2 * per_flux_eval
+    per_point = 40 + 2 * cost["log"] + 2 * cost["rcp"]
+    return nbr * per_nbr + stencils * per_stencil + cloud.n * per_point, cost
+
+
+def run_ours(args, rank, world, local):
+    import torch
+
+    from paper_2108_07031_gb300 import lskum as L
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    cloud = _cloud(args.points)
+    n = cloud.n
+    stream = torch.cuda.Stream()
+    solver = L.Solver.from_cloud(cloud)
+    solver.set_stream(stream.cuda_stream)
+    solver.set_freestream(MACH, ALPHA)
+    info = solver.info()
+
+    # warm-up (also captures the iteration graph)
+    solver.step(args.warmup)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # timed region: K iterations, per-kernel CUDA events on the solver's stream
+    solver.profile(True)
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        start.record(stream)
+        solver.step(args.steps)
+        launches = solver.last_launch_count()
+        end.record(stream)
+        barrier()
+    ms = start.elapsed_time(end)
+    flux_ms, flux_n = solver.kernel_time(L.KERNEL_FLUX)
+    kt = {name: solver.kernel_time(k) for name, k in (("flux", L.KERNEL_FLUX),
+                                                       ("ls_first", L.KERNEL_LS_FIRST),
+                                                       ("ls_inner", L.KERNEL_LS_INNER),
+                                                       ("residue", L.KERNEL_REDUCE))}
+    solver.profile(False)
+    clocks = clk.summary()
+    t_max = ms
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = world * n * args.steps / (t_max * 1e-3)
+
+    # end to end through the C ABI with host buffers: H2D of the state,
+    # one iteration, D2H of the residue, every step
+    W0 = solver.get_state()
+    pinned = torch.from_numpy(W0).pin_memory()
+    e2e_steps = max(1, min(args.steps, 5))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        solver.set_state_ptr(pinned.data_ptr())
+        solver.step(1)
+        _ = solver.residual_norm()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    e2e_t = e2e_s
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_t = float(t.item())
+    e2e_value = world * n * e2e_steps / e2e_t
+
+    result = None
+    if rank == 0:
+        peaks = _fp64_peak()
+        work, cost = fp64_work_per_launch(cloud, peaks)
+        flux_launch_ms = flux_ms / max(flux_n, 1)
+        achieved = work / (flux_launch_ms * 1e-3) / 1e12
+        peak = peaks.get("fp64_fma_tflops")
+        mp, mp_kind = _peaks()
+        hbm_bytes_per_pt_it = 4600.0  # algorithmic bytes per point-iteration (minimal passes)
+        cpu = cpu_baseline(args) if not args.no_cpu_baseline else None
+        result = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "ours",
+            "config": {"workload": f"naca0012-o-cloud-{n}pts-fp64", "points": n,
+                       "mach": MACH, "alpha_deg": ALPHA, "inner_iters": 2, "rk_stages": 4,
+                       "cfl": 0.2, "max_neighbours": info["max_neighbours"],
+                       "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (device working set ~12 GB), no flush"},
+            "roofline": {
+                "kernel": "k_flux (flux residual + SSP-RK stage update)", "bound": "alu",
+                "unit": "TFLOP/s", "achieved": achieved, "peak": peak,
+                "frac": (achieved / peak) if peak else None, "traffic": None,
+                "peak_source": "measured FP64 FMA rate of pipe_peaks on this GPU "
+                               "(nominal 1.25 TFLOP/s)",
+                "flop_equivalents_per_launch": work, "launch_ms": flux_launch_ms,
+                "hbm_frac_of_measured": (hbm_bytes_per_pt_it * n / (t_max / args.steps * 1e-3))
+                / (mp["hbm_gbs"] * 1e9), "hbm_peak_kind": mp_kind,
+            },
+            "kernel_ms": {k: {"total_ms": v[0], "launches": v[1]} for k, v in kt.items()},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n * 32,
+                    "d2h_bytes_per_step": 8, "steps": e2e_steps},
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+    solver.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return result
+
+
+def _oracle_sample_rate(iters: int):
+    """Oracle pt-it/s on the 2.5M-point cloud of the same family (one iteration = one step)."""
+    from oracle import oracle as O
+    cloud = _cloud(SAMPLE_POINTS)
+    oc = O.OracleCloud.from_cloud(cloud)
+    W = np.tile(O.freestream(MACH, ALPHA), (cloud.n, 1))
+    t0 = time.perf_counter()
+    W, res, st = O.iterate(oc, W, iters)
+    dt = time.perf_counter() - t0
+    return cloud.n * iters / dt, O.num_threads(), cloud.n
+
+
+def cpu_baseline(args):
+    rate, cores, n = _oracle_sample_rate(2)
+    return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"2 iterations of the FP64 CPU oracle on the {n}-point cloud of the same "
+                      f"NACA 0012 family (the 10M workload's distribution at 1/4 the points)"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    from oracle import oracle as O
+    cloud = _cloud(SAMPLE_POINTS)
+    oc = O.OracleCloud.from_cloud(cloud)
+    W = np.tile(O.freestream(MACH, ALPHA), (cloud.n, 1))
+    for _ in range(args.warmup):
+        W, _, _ = O.iterate(oc, W, 1)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        W, _, _ = O.iterate(oc, W, 1)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = cloud.n * args.steps / total
+    cores = O.num_threads()
+    sample = (f"1 oracle iteration per step on the {cloud.n}-point cloud of the same NACA 0012 "
+              f"family (the 10M workload's distribution at 1/4 the points)")
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "impl": "reference",
+        "config": {"workload": "naca0012-o-cloud-10003344pts-fp64", "points": WORKLOAD_POINTS,
+                   "mach": MACH, "alpha_deg": ALPHA, "inner_iters": 2, "rk_stages": 4,
+                   "cfl": 0.2, "parallelism": "host cores"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": cores,
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--points", type=int, default=WORKLOAD_POINTS)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)  # at least three untimed warm-up steps
+    args.steps = max(args.steps, 1)
+    rank, world, local = _dist()
+    if args.impl == "reference":
+        res = run_reference(args, rank, world)
+    else:
+        res = run_ours(args, rank, world, local)
+    if rank == 0 and res is not None:
+        print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

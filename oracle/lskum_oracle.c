@@ -162,6 +162,28 @@ void orc_split_flux(const double* W, int dir, int sign, double gamma, double* G)
     G[3] = g_e;
 }
 
+/* Array forms of the point maps (n rows of 4). */
+void orc_prim_to_q_n(int64_t n, const double* W, double gamma, double* q) {
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) orc_prim_to_q(W + 4 * i, gamma, q + 4 * i);
+}
+void orc_q_to_prim_n(int64_t n, const double* q, double gamma, double* W) {
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) orc_q_to_prim(q + 4 * i, gamma, W + 4 * i);
+}
+void orc_prim_to_cons_n(int64_t n, const double* W, double gamma, double* U) {
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) orc_prim_to_cons(W + 4 * i, gamma, U + 4 * i);
+}
+void orc_cons_to_prim_n(int64_t n, const double* U, double gamma, double* W) {
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) orc_cons_to_prim(U + 4 * i, gamma, W + 4 * i);
+}
+void orc_split_flux_n(int64_t n, const double* W, int dir, int sign, double gamma, double* G) {
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) orc_split_flux(W + 4 * i, dir, sign, gamma, G + 4 * i);
+}
+
 /* ---------------------------------------------------------- q-derivatives */
 
 /* One least-squares sweep over the full stencil, global frame. With px, py

@@ -59,6 +59,10 @@ def _load():
             lib.orc_prim_to_cons.argtypes = [P, C.c_double, P]
             lib.orc_cons_to_prim.argtypes = [P, C.c_double, P]
             lib.orc_split_flux.argtypes = [P, C.c_int, C.c_int, C.c_double, P]
+            for nm in ("orc_prim_to_q_n", "orc_q_to_prim_n", "orc_prim_to_cons_n",
+                       "orc_cons_to_prim_n"):
+                getattr(lib, nm).argtypes = [C.c_int64, P, C.c_double, P]
+            lib.orc_split_flux_n.argtypes = [C.c_int64, P, C.c_int, C.c_int, C.c_double, P]
             lib.orc_q_derivatives.argtypes = [P, P, C.c_int, P, P]
             lib.orc_ls_sweep.argtypes = [P, P, P, P, P, P]
             lib.orc_flux_residual.argtypes = [P, P, P, P, P]
@@ -131,8 +135,7 @@ def prim_to_q(W, gamma=GAMMA):
     lib = _load()
     W = _f64(W, (-1, 4))
     q = np.empty_like(W)
-    for i in range(W.shape[0]):
-        lib.orc_prim_to_q(_ptr(W[i]), gamma, _ptr(q[i]))
+    lib.orc_prim_to_q_n(W.shape[0], _ptr(W), float(gamma), _ptr(q))
     return q
 
 
@@ -141,8 +144,7 @@ def q_to_prim(q, gamma=GAMMA):
     lib = _load()
     q = _f64(q, (-1, 4))
     W = np.empty_like(q)
-    for i in range(q.shape[0]):
-        lib.orc_q_to_prim(_ptr(q[i]), gamma, _ptr(W[i]))
+    lib.orc_q_to_prim_n(q.shape[0], _ptr(q), float(gamma), _ptr(W))
     return W
 
 
@@ -150,8 +152,7 @@ def prim_to_cons(W, gamma=GAMMA):
     lib = _load()
     W = _f64(W, (-1, 4))
     U = np.empty_like(W)
-    for i in range(W.shape[0]):
-        lib.orc_prim_to_cons(_ptr(W[i]), gamma, _ptr(U[i]))
+    lib.orc_prim_to_cons_n(W.shape[0], _ptr(W), float(gamma), _ptr(U))
     return U
 
 
@@ -159,8 +160,7 @@ def cons_to_prim(U, gamma=GAMMA):
     lib = _load()
     U = _f64(U, (-1, 4))
     W = np.empty_like(U)
-    for i in range(U.shape[0]):
-        lib.orc_cons_to_prim(_ptr(U[i]), gamma, _ptr(W[i]))
+    lib.orc_cons_to_prim_n(U.shape[0], _ptr(U), float(gamma), _ptr(W))
     return W
 
 
@@ -169,8 +169,7 @@ def split_flux(W, direction: int, sign: int, gamma=GAMMA):
     lib = _load()
     W = _f64(W, (-1, 4))
     G = np.empty_like(W)
-    for i in range(W.shape[0]):
-        lib.orc_split_flux(_ptr(W[i]), int(direction), int(sign), gamma, _ptr(G[i]))
+    lib.orc_split_flux_n(W.shape[0], _ptr(W), int(direction), int(sign), float(gamma), _ptr(G))
     return G
 
 

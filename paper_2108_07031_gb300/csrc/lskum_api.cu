@@ -1,0 +1,574 @@
+// C ABI of the solver (include/lskum.h): context life cycle, device memory,
+// the pseudo-time iteration of Algorithm 1 as kernel launches (captured once
+// into a CUDA graph and replayed), state transfer and diagnostics.
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lskum_internal.h"
+#include "lskum_kernels.cuh"
+
+using namespace lskum;
+
+namespace lskum {
+namespace {
+thread_local std::string g_last_error;
+}
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+static const char* last_error_cstr() { return g_last_error.c_str(); }
+}  // namespace lskum
+
+namespace {
+
+constexpr int64_t kResCap = 1 << 20;
+constexpr double kPi = 3.14159265358979323846;
+
+struct Timer {
+    std::vector<cudaEvent_t> ev;  // pairs
+    double total_ms = 0.0;
+    int64_t launches = 0;
+};
+
+}  // namespace
+
+struct lskum_ctx {
+    lskum_options opt{};
+    int device = 0;
+    cudaStream_t own_stream = nullptr;
+    cudaStream_t stream = nullptr;
+    int block = kDefaultBlock;
+
+    HostLayout host;
+    DevGeom g{};
+    Physics ph{};
+    DevState st{};
+    std::vector<void*> allocations;
+
+    V4* staging = nullptr;  // n x 4 in caller order (state transfer)
+    V8* staging8 = nullptr; // n x 8 in caller order (derivative output)
+    int* h_status = nullptr;             // pinned
+    double* h_small = nullptr;           // pinned scratch for small reads
+
+    bool have_state = false;
+    double mach = 0.0, alpha = 0.0;
+    int64_t iters_done = 0;  // iterations since the last state reset
+
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    bool use_graph = true;
+
+    bool profiling = false;
+    Timer timers[kNumKernelClasses];
+    int64_t last_launches = 0;
+};
+
+namespace {
+
+int fail(int code, const std::string& msg) {
+    set_last_error(msg);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    return fail(LSKUM_ERR_CUDA, m);
+}
+
+#define LSKUM_CUDA(call)                                        \
+    do {                                                        \
+        cudaError_t e_ = (call);                                \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);     \
+    } while (0)
+
+template <typename T>
+cudaError_t dev_alloc(lskum_ctx* c, T** p, size_t count) {
+    void* raw = nullptr;
+    cudaError_t e = cudaMalloc(&raw, std::max<size_t>(count, 1) * sizeof(T));
+    if (e == cudaSuccess) c->allocations.push_back(raw);
+    *p = static_cast<T*>(raw);
+    return e;
+}
+
+template <typename T>
+cudaError_t upload(lskum_ctx* c, const T** dst, const std::vector<T>& src) {
+    T* p = nullptr;
+    cudaError_t e = dev_alloc(c, &p, src.size());
+    if (e != cudaSuccess) return e;
+    if (!src.empty()) e = cudaMemcpy(p, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+    *dst = p;
+    return e;
+}
+
+void release(lskum_ctx* c) {
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    for (auto& t : c->timers)
+        for (auto e : t.ev) cudaEventDestroy(e);
+    for (void* p : c->allocations) cudaFree(p);
+    if (c->h_status) cudaFreeHost(c->h_status);
+    if (c->h_small) cudaFreeHost(c->h_small);
+    if (c->own_stream) cudaStreamDestroy(c->own_stream);
+}
+
+// Kernel launch wrapper that records CUDA events around a launch while
+// profiling is on (one event pair per launch; resolved in lskum_kernel_time).
+template <typename F>
+cudaError_t timed(lskum_ctx* c, int cls, F&& launch) {
+    if (!c->profiling) return launch();
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, c->stream);
+    cudaError_t e = launch();
+    cudaEventRecord(b, c->stream);
+    c->timers[cls].ev.push_back(a);
+    c->timers[cls].ev.push_back(b);
+    return e;
+}
+
+int n_blocks(const lskum_ctx* c) { return int((c->g.n + c->block - 1) / c->block); }
+
+// q-derivatives of st.q[0] into st.dq[final]; returns the index of the buffer
+// holding the result.
+cudaError_t run_q_derivatives(lskum_ctx* c, const V4* q, int* final_buf, int64_t* launches) {
+    cudaError_t e = timed(c, kLsFirst, [&] { return launch_ls_first(c->g, q, c->st.dq[0], c->block, c->stream); });
+    if (e != cudaSuccess) return e;
+    ++*launches;
+    int cur = 0;
+    for (int it = 0; it < c->opt.inner_iters; ++it) {
+        e = timed(c, kLsInner, [&] {
+            return launch_ls_inner(c->g, q, c->st.dq[cur], c->st.dq[1 - cur], c->block, c->stream);
+        });
+        if (e != cudaSuccess) return e;
+        ++*launches;
+        cur = 1 - cur;
+    }
+    *final_buf = cur;
+    return cudaSuccess;
+}
+
+// One pseudo-time iteration (Algorithm 1): four stages of q-derivatives and
+// fused flux/update, then the residue. Starts and ends with q in st.q[0].
+cudaError_t run_iteration(lskum_ctx* c, int64_t* launches) {
+    int qcur = 0;
+    for (int stage = 1; stage <= 4; ++stage) {
+        int dbuf = 0;
+        cudaError_t e = run_q_derivatives(c, c->st.q[qcur], &dbuf, launches);
+        if (e != cudaSuccess) return e;
+        e = timed(c, kFlux, [&] {
+            return launch_flux(stage, c->g, c->ph, c->st, c->st.q[qcur], c->st.dq[dbuf],
+                               c->st.q[1 - qcur], c->block, c->stream);
+        });
+        if (e != cudaSuccess) return e;
+        ++*launches;
+        qcur = 1 - qcur;
+        if (stage == 1) {
+            e = timed(c, kReduce, [&] { return launch_residue(c->st, n_blocks(c), c->g.n, c->stream); });
+            if (e != cudaSuccess) return e;
+            ++*launches;
+        }
+    }
+    return cudaSuccess;
+}
+
+int reset_history(lskum_ctx* c) {
+    LSKUM_CUDA(cudaMemsetAsync(c->st.iter_counter, 0, sizeof(unsigned long long), c->stream));
+    LSKUM_CUDA(cudaMemsetAsync(c->st.status, 0, sizeof(int), c->stream));
+    c->iters_done = 0;
+    return LSKUM_OK;
+}
+
+int read_status(lskum_ctx* c, int* status) {
+    LSKUM_CUDA(cudaMemcpyAsync(c->h_status, c->st.status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    LSKUM_CUDA(cudaStreamSynchronize(c->stream));
+    *status = *c->h_status;
+    return LSKUM_OK;
+}
+
+int read_residue(lskum_ctx* c, int64_t iter, double* out) {
+    const int64_t slot = iter % kResCap;
+    LSKUM_CUDA(cudaMemcpyAsync(c->h_small, c->st.res_hist + slot, sizeof(double),
+                               cudaMemcpyDeviceToHost, c->stream));
+    LSKUM_CUDA(cudaStreamSynchronize(c->stream));
+    *out = *c->h_small;
+    return LSKUM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lskum_default_options(lskum_options* o) {
+    if (!o) return fail(LSKUM_ERR_INVALID_ARG, "null options");
+    o->gamma = 1.4;
+    o->cfl = 0.2;
+    o->inner_iters = 2;
+    o->order = 2;
+    o->wall_factor = 2.0;
+    o->outer_mode = LSKUM_OUTER_FREESTREAM;
+    o->precision = LSKUM_FP64;
+    o->reorder = 1;
+    o->block_size = 0;
+    o->check_every = 50;
+    return LSKUM_OK;
+}
+
+int lskum_create(int64_t n, const double* xy, const double* normals, const int8_t* flags,
+                 const int32_t* nbr_offsets, const int32_t* nbr_idx, const lskum_options* opt,
+                 lskum_ctx** out) {
+    if (!out) return fail(LSKUM_ERR_INVALID_ARG, "null output pointer");
+    *out = nullptr;
+    lskum_options o;
+    lskum_default_options(&o);
+    if (opt) o = *opt;
+    if (!(o.gamma > 1.0 && o.gamma < 2.0) || !(o.cfl > 0.0) || o.inner_iters < 0 ||
+        o.inner_iters > 64 || (o.order != 1 && o.order != 2) || !(o.wall_factor > 0.0) ||
+        (o.outer_mode != 0 && o.outer_mode != 1) || o.precision != LSKUM_FP64 ||
+        (o.block_size != 0 && o.block_size != 128 && o.block_size != 256) || o.check_every < 1)
+        return fail(LSKUM_ERR_INVALID_ARG, "invalid option value");
+
+    lskum_ctx* c = new (std::nothrow) lskum_ctx();
+    if (!c) return fail(LSKUM_ERR_INVALID_ARG, "out of host memory");
+    c->opt = o;
+    c->block = o.block_size ? o.block_size : kDefaultBlock;
+
+    // host validation and layout first: input errors are reported without a GPU
+    std::string err;
+    int rc = build_layout(n, xy, normals, flags, nbr_offsets, nbr_idx, o, c->host, err);
+    if (rc != LSKUM_OK) {
+        delete c;
+        return fail(rc, err);
+    }
+    int ndev = 0;
+    cudaError_t ce = cudaGetDeviceCount(&ndev);
+    if (ce != cudaSuccess || ndev == 0) {
+        delete c;
+        return fail(LSKUM_ERR_CUDA, std::string("no usable CUDA device: ") +
+                                        (ce != cudaSuccess ? cudaGetErrorString(ce) : "none found"));
+    }
+    cudaGetDevice(&c->device);
+    auto bail = [&](cudaError_t e, const char* where) {
+        release(c);
+        delete c;
+        return cuda_fail(e, where);
+    };
+    cudaError_t e;
+    if ((e = cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking)) != cudaSuccess)
+        return bail(e, "cudaStreamCreate");
+    c->stream = c->own_stream;
+
+    const HostLayout& L = c->host;
+    DevGeom& g = c->g;
+    g.n = L.n;
+    g.stride = L.stride;
+    g.slots = L.slots;
+    g.n_wall = int64_t(L.wall_id.size());
+    std::vector<double2> nrm2(L.n), nds2(L.wall_id.size());
+    for (int64_t i = 0; i < L.n; ++i) nrm2[i] = make_double2(L.nrm[2 * i], L.nrm[2 * i + 1]);
+    for (size_t k = 0; k < L.wall_id.size(); ++k) nds2[k] = make_double2(L.wall_nds[2 * k], L.wall_nds[2 * k + 1]);
+    if ((e = upload(c, &g.cnt, L.cnt)) != cudaSuccess ||
+        (e = upload(c, &g.flag, L.flag)) != cudaSuccess ||
+        (e = upload(c, &g.nrm, nrm2)) != cudaSuccess ||
+        (e = upload(c, &g.dmin, L.dmin)) != cudaSuccess ||
+        (e = upload(c, &g.nbr, L.nbr)) != cudaSuccess ||
+        (e = upload(c, &g.hdx, L.hdx)) != cudaSuccess ||
+        (e = upload(c, &g.hdy, L.hdy)) != cudaSuccess ||
+        (e = upload(c, &g.wx, L.wx)) != cudaSuccess ||
+        (e = upload(c, &g.wy, L.wy)) != cudaSuccess ||
+        (e = upload(c, &g.ws, L.ws)) != cudaSuccess ||
+        (e = upload(c, &g.wn, L.wn)) != cudaSuccess ||
+        (e = upload(c, &g.dev_to_user, L.dev_to_user)) != cudaSuccess ||
+        (e = upload(c, &g.user_to_dev, L.user_to_dev)) != cudaSuccess ||
+        (e = upload(c, &g.wall_id, L.wall_id)) != cudaSuccess ||
+        (e = upload(c, &g.wall_nds, nds2)) != cudaSuccess)
+        return bail(e, "upload of the cloud layout");
+
+    DevState& st = c->st;
+    const size_t N = size_t(L.n);
+    const int nb = int((L.n + 127) / 128) + 1;  // enough for either block size
+    if ((e = dev_alloc(c, &st.U, N)) != cudaSuccess || (e = dev_alloc(c, &st.U0, N)) != cudaSuccess ||
+        (e = dev_alloc(c, &st.q[0], N)) != cudaSuccess || (e = dev_alloc(c, &st.q[1], N)) != cudaSuccess ||
+        (e = dev_alloc(c, &st.dq[0], N)) != cudaSuccess || (e = dev_alloc(c, &st.dq[1], N)) != cudaSuccess ||
+        (e = dev_alloc(c, &st.dt, N)) != cudaSuccess || (e = dev_alloc(c, &st.R, N)) != cudaSuccess ||
+        (e = dev_alloc(c, &st.partials, size_t(nb))) != cudaSuccess ||
+        (e = dev_alloc(c, &st.res_hist, size_t(kResCap))) != cudaSuccess ||
+        (e = dev_alloc(c, &st.iter_counter, 1)) != cudaSuccess ||
+        (e = dev_alloc(c, &st.status, 1)) != cudaSuccess ||
+        (e = dev_alloc(c, &st.force_out, 2)) != cudaSuccess ||
+        (e = dev_alloc(c, &c->staging, N)) != cudaSuccess)
+        return bail(e, "device state allocation");
+    st.res_cap = kResCap;
+    if ((e = cudaMallocHost(&c->h_status, sizeof(int) * 4)) != cudaSuccess ||
+        (e = cudaMallocHost(&c->h_small, sizeof(double) * 4)) != cudaSuccess)
+        return bail(e, "pinned host allocation");
+
+    Physics& ph = c->ph;
+    ph.gamma = o.gamma;
+    ph.gm1 = o.gamma - 1.0;
+    ph.gm1_inv = 1.0 / (o.gamma - 1.0);
+    ph.cfl = o.cfl;
+    ph.p_inf = 1.0 / o.gamma;
+    ph.order = o.order;
+    ph.outer_fixed = o.outer_mode == LSKUM_OUTER_FREESTREAM ? 1 : 0;
+
+    if ((e = cudaMemsetAsync(st.iter_counter, 0, sizeof(unsigned long long), c->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(st.status, 0, sizeof(int), c->stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
+        return bail(e, "initialisation");
+    *out = c;
+    return LSKUM_OK;
+}
+
+void lskum_destroy(lskum_ctx* c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    release(c);
+    delete c;
+}
+
+int lskum_set_stream(lskum_ctx* c, void* stream) {
+    if (!c) return fail(LSKUM_ERR_INVALID_ARG, "null context");
+    LSKUM_CUDA(cudaStreamSynchronize(c->stream));
+    c->stream = stream ? static_cast<cudaStream_t>(stream) : c->own_stream;
+    return LSKUM_OK;
+}
+
+int lskum_set_freestream(lskum_ctx* c, double mach, double alpha_deg) {
+    if (!c) return fail(LSKUM_ERR_INVALID_ARG, "null context");
+    if (!(mach >= 0.0) || !std::isfinite(mach) || !std::isfinite(alpha_deg))
+        return fail(LSKUM_ERR_INVALID_ARG, "invalid free stream");
+    c->mach = mach;
+    c->alpha = alpha_deg;
+    const double a = alpha_deg * kPi / 180.0;
+    const V4 W{1.0, mach * std::cos(a), mach * std::sin(a), 1.0 / c->opt.gamma};
+    LSKUM_CUDA(launch_set_uniform(c->g, c->ph, W, c->st.U, c->st.q[0], c->stream));
+    int rc = reset_history(c);
+    if (rc != LSKUM_OK) return rc;
+    c->have_state = true;
+    return LSKUM_OK;
+}
+
+int lskum_set_state(lskum_ctx* c, const double* prim) {
+    if (!c || !prim) return fail(LSKUM_ERR_INVALID_ARG, "null argument");
+    LSKUM_CUDA(cudaMemcpyAsync(c->staging, prim, sizeof(V4) * size_t(c->g.n), cudaMemcpyHostToDevice, c->stream));
+    int rc = reset_history(c);
+    if (rc != LSKUM_OK) return rc;
+    LSKUM_CUDA(launch_set_prim(c->g, c->ph, c->staging, c->st.U, c->st.q[0], c->st.status, c->stream));
+    int status = 0;
+    rc = read_status(c, &status);
+    if (rc != LSKUM_OK) return rc;
+    if (status) {
+        reset_history(c);
+        c->have_state = false;
+        return fail(LSKUM_ERR_DIVERGED, "state has a non-finite value or rho <= 0 or p <= 0");
+    }
+    c->have_state = true;
+    return LSKUM_OK;
+}
+
+int lskum_get_state(lskum_ctx* c, double* prim) {
+    if (!c || !prim) return fail(LSKUM_ERR_INVALID_ARG, "null argument");
+    if (!c->have_state) return fail(LSKUM_ERR_STATE, "no state set");
+    LSKUM_CUDA(launch_get_prim(c->g, c->ph, c->st.U, c->staging, c->stream));
+    LSKUM_CUDA(cudaMemcpyAsync(prim, c->staging, sizeof(V4) * size_t(c->g.n), cudaMemcpyDeviceToHost, c->stream));
+    LSKUM_CUDA(cudaStreamSynchronize(c->stream));
+    return LSKUM_OK;
+}
+
+int lskum_step(lskum_ctx* c, int n_iters) {
+    if (!c || n_iters < 0) return fail(LSKUM_ERR_INVALID_ARG, "invalid argument");
+    if (!c->have_state) return fail(LSKUM_ERR_STATE, "no state set");
+    int64_t launches = 0;
+    const bool graph = c->use_graph && !c->profiling;
+    if (graph && !c->graph_exec && n_iters > 0) {
+        int64_t cap_launches = 0;
+        LSKUM_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = run_iteration(c, &cap_launches);
+        cudaGraph_t gr = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(c->stream, &gr);
+        if (e != cudaSuccess) return cuda_fail(e, "iteration capture");
+        if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+        c->graph = gr;
+        LSKUM_CUDA(cudaGraphInstantiate(&c->graph_exec, c->graph, 0));
+    }
+    for (int it = 0; it < n_iters; ++it) {
+        if (graph) {
+            LSKUM_CUDA(cudaGraphLaunch(c->graph_exec, c->stream));
+            launches += 4 * (2 + c->opt.inner_iters) + 1;
+        } else {
+            cudaError_t e = run_iteration(c, &launches);
+            if (e != cudaSuccess) return cuda_fail(e, "iteration launch");
+        }
+    }
+    c->iters_done += n_iters;
+    c->last_launches = launches;
+    int status = 0;
+    int rc = read_status(c, &status);
+    if (rc != LSKUM_OK) return rc;
+    if (status) return fail(LSKUM_ERR_DIVERGED, "non-finite or non-physical state during iteration");
+    return LSKUM_OK;
+}
+
+int lskum_solve(lskum_ctx* c, int max_iters, double tol, int* iters_done) {
+    if (!c || max_iters < 0 || !(tol > 0.0)) return fail(LSKUM_ERR_INVALID_ARG, "invalid argument");
+    if (iters_done) *iters_done = 0;
+    int done = 0;
+    double first = 0.0;
+    int64_t first_iter = c->iters_done;
+    while (done < max_iters) {
+        const int chunk = std::min(c->opt.check_every, max_iters - done);
+        int rc = lskum_step(c, chunk);
+        done += chunk;
+        if (iters_done) *iters_done = done;
+        if (rc != LSKUM_OK) return rc;
+        if (first == 0.0) {
+            // first non-zero residue of this run
+            for (int64_t k = first_iter; k < c->iters_done && first == 0.0; ++k) {
+                double r = 0.0;
+                rc = read_residue(c, k, &r);
+                if (rc != LSKUM_OK) return rc;
+                if (r > 0.0) first = r;
+            }
+            first_iter = c->iters_done;
+        }
+        double last = 0.0;
+        rc = read_residue(c, c->iters_done - 1, &last);
+        if (rc != LSKUM_OK) return rc;
+        if (first > 0.0 && last <= tol * first) break;
+    }
+    return LSKUM_OK;
+}
+
+int lskum_residual_norm(lskum_ctx* c, double* out) {
+    if (!c || !out) return fail(LSKUM_ERR_INVALID_ARG, "null argument");
+    if (c->iters_done == 0) {
+        *out = 0.0;
+        return LSKUM_OK;
+    }
+    return read_residue(c, c->iters_done - 1, out);
+}
+
+int lskum_forces(lskum_ctx* c, double* cl, double* cd) {
+    if (!c || !cl || !cd) return fail(LSKUM_ERR_INVALID_ARG, "null argument");
+    if (!c->have_state) return fail(LSKUM_ERR_STATE, "no state set");
+    LSKUM_CUDA(launch_forces(c->g, c->ph, c->st, c->stream));
+    LSKUM_CUDA(cudaMemcpyAsync(c->h_small, c->st.force_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    LSKUM_CUDA(cudaStreamSynchronize(c->stream));
+    const double fx = c->h_small[0], fy = c->h_small[1];
+    const double a = c->alpha * kPi / 180.0;
+    const double qinf = 0.5 * c->mach * c->mach;
+    if (!(qinf > 0.0)) return fail(LSKUM_ERR_STATE, "forces need a free stream with M > 0");
+    *cl = (-fx * std::sin(a) + fy * std::cos(a)) / qinf;
+    *cd = (fx * std::cos(a) + fy * std::sin(a)) / qinf;
+    return LSKUM_OK;
+}
+
+int lskum_eval_residual(lskum_ctx* c, double* R) {
+    if (!c || !R) return fail(LSKUM_ERR_INVALID_ARG, "null argument");
+    if (!c->have_state) return fail(LSKUM_ERR_STATE, "no state set");
+    int dbuf = 0;
+    int64_t launches = 0;
+    cudaError_t e = run_q_derivatives(c, c->st.q[0], &dbuf, &launches);
+    if (e != cudaSuccess) return cuda_fail(e, "q-derivatives");
+    LSKUM_CUDA(launch_flux(0, c->g, c->ph, c->st, c->st.q[0], c->st.dq[dbuf], nullptr, c->block, c->stream));
+    LSKUM_CUDA(launch_gather_v4(c->g, c->st.R, c->staging, c->stream));
+    LSKUM_CUDA(cudaMemcpyAsync(R, c->staging, sizeof(V4) * size_t(c->g.n), cudaMemcpyDeviceToHost, c->stream));
+    LSKUM_CUDA(cudaStreamSynchronize(c->stream));
+    return LSKUM_OK;
+}
+
+int lskum_eval_q_derivatives(lskum_ctx* c, double* qx, double* qy) {
+    if (!c || !qx || !qy) return fail(LSKUM_ERR_INVALID_ARG, "null argument");
+    if (!c->have_state) return fail(LSKUM_ERR_STATE, "no state set");
+    if (!c->staging8) {
+        LSKUM_CUDA(dev_alloc(c, &c->staging8, size_t(c->g.n)));
+    }
+    int dbuf = 0;
+    int64_t launches = 0;
+    cudaError_t e = run_q_derivatives(c, c->st.q[0], &dbuf, &launches);
+    if (e != cudaSuccess) return cuda_fail(e, "q-derivatives");
+    LSKUM_CUDA(launch_gather_v8(c->g, c->st.dq[dbuf], c->staging8, c->stream));
+    std::vector<V8> h(size_t(c->g.n));
+    LSKUM_CUDA(cudaMemcpyAsync(h.data(), c->staging8, sizeof(V8) * h.size(), cudaMemcpyDeviceToHost, c->stream));
+    LSKUM_CUDA(cudaStreamSynchronize(c->stream));
+    for (size_t i = 0; i < h.size(); ++i)
+        for (int m = 0; m < 4; ++m) {
+            qx[4 * i + m] = h[i].x[m];
+            qy[4 * i + m] = h[i].y[m];
+        }
+    return LSKUM_OK;
+}
+
+int lskum_info(lskum_ctx* c, int64_t* n_points, int64_t* n_wall, int* max_neighbours) {
+    if (!c) return fail(LSKUM_ERR_INVALID_ARG, "null context");
+    if (n_points) *n_points = c->g.n;
+    if (n_wall) *n_wall = c->g.n_wall;
+    if (max_neighbours) *max_neighbours = c->g.slots;
+    return LSKUM_OK;
+}
+
+static int resolve_timers(lskum_ctx* c) {
+    LSKUM_CUDA(cudaStreamSynchronize(c->stream));
+    for (auto& t : c->timers) {
+        for (size_t k = 0; k + 1 < t.ev.size(); k += 2) {
+            float ms = 0.f;
+            LSKUM_CUDA(cudaEventElapsedTime(&ms, t.ev[k], t.ev[k + 1]));
+            t.total_ms += ms;
+            t.launches += 1;
+            cudaEventDestroy(t.ev[k]);
+            cudaEventDestroy(t.ev[k + 1]);
+        }
+        t.ev.clear();
+    }
+    return LSKUM_OK;
+}
+
+int lskum_profile(lskum_ctx* c, int enable) {
+    if (!c) return fail(LSKUM_ERR_INVALID_ARG, "null context");
+    int rc = resolve_timers(c);
+    if (rc != LSKUM_OK) return rc;
+    if (enable) {
+        for (auto& t : c->timers) {
+            t.total_ms = 0.0;
+            t.launches = 0;
+        }
+    }
+    c->profiling = enable != 0;
+    return LSKUM_OK;
+}
+
+int lskum_kernel_time(lskum_ctx* c, int kernel, double* total_ms, int64_t* launches) {
+    if (!c || kernel < 0 || kernel >= kNumKernelClasses)
+        return fail(LSKUM_ERR_INVALID_ARG, "invalid argument");
+    int rc = resolve_timers(c);
+    if (rc != LSKUM_OK) return rc;
+    if (total_ms) *total_ms = c->timers[kernel].total_ms;
+    if (launches) *launches = c->timers[kernel].launches;
+    return LSKUM_OK;
+}
+
+int64_t lskum_last_launch_count(lskum_ctx* c) { return c ? c->last_launches : -1; }
+
+const char* lskum_error_string(int code) {
+    switch (code) {
+        case LSKUM_OK: return "ok";
+        case LSKUM_ERR_INVALID_ARG: return "invalid argument";
+        case LSKUM_ERR_BAD_CONNECTIVITY: return "bad connectivity";
+        case LSKUM_ERR_DEGENERATE_STENCIL: return "degenerate stencil";
+        case LSKUM_ERR_CUDA: return "CUDA error";
+        case LSKUM_ERR_DIVERGED: return "diverged";
+        case LSKUM_ERR_TIMEOUT: return "timeout";
+        case LSKUM_ERR_STATE: return "call out of order";
+        default: return "unknown error";
+    }
+}
+
+const char* lskum_last_error(void) { return lskum::last_error_cstr(); }
+
+}  // extern "C"

@@ -1,0 +1,482 @@
+// FP64 device kernels of the q-LSKUM hot path (sm_103a).
+//
+// Mapping: one thread per point, points in Hilbert-curve order (set-up), so a
+// warp's 32 points and their stencils are spatially close. Per-slot data
+// (packed neighbour entry, half offsets, least-squares weights) is slot-major
+// [slot][point]: consecutive threads read consecutive words (coalesced). The
+// gathered per-point records are AoS: q (32 B) and (q_x, q_y) (64 B), so a
+// neighbour gather is one or two full sectors.
+//
+// Per stage (Algorithm 2 re-fused):
+//   ls_first  : q_x, q_y from Eq. 11 (full stencil), weights precomputed
+//   ls_inner  : Jacobi sweep of Eq. 29 with dq~ of Eq. 28 (x inner_iters)
+//   flux<k>   : residual of Eq. 12 -- per neighbour q~_j and q~_0 (Eq. 28),
+//               their primitive states, the kinetic split fluxes G+-(q~)
+//               along s and n (Eq. 27), accumulated with the precomputed
+//               split-stencil weights (Eq. 24 over the Eq. 14 stencils) --
+//               fused with the SSP-RK stage update, the wall condition, the
+//               next stage's q-variables (Eq. 26), the stage-1 local time
+//               step and the stage-1 partial sums of the residue.
+//   residue   : fixed-order reduction of the partial sums (deterministic).
+//
+// The arithmetic is FP64 throughout. On GB300 the FP64 pipe, not HBM,
+// bounds the flux kernel.
+
+#include <cmath>
+
+#include "lskum_internal.h"
+#include "lskum_kernels.cuh"
+
+namespace lskum {
+
+namespace {
+
+constexpr double kInvSqrtPi = 0.56418958354775628695;  // 1 / sqrt(pi)
+
+__device__ __forceinline__ V4 ld4(const V4* p) { return *p; }
+
+struct Prim {
+    double r, u, v, p, beta, sb;  // density, velocity (frame components), pressure, beta, sqrt(beta)
+};
+
+// q -> primitive (inverse of Eq. 26); velocities in the global frame.
+__device__ __forceinline__ Prim q_to_prim(const double t0, const double t1, const double t2,
+                                          const double t3, const double gm1_inv) {
+    Prim w;
+    const double beta = -0.5 * t3;
+    const double inv2b = -1.0 / t3;  // 1 / (2 beta)
+    w.u = t1 * inv2b;
+    w.v = t2 * inv2b;
+    w.r = exp(t0 - log(beta) * gm1_inv + beta * (w.u * w.u + w.v * w.v));
+    w.p = w.r * inv2b;
+    w.beta = beta;
+    w.sb = sqrt(beta);
+    return w;
+}
+
+// Kinetic split flux along the frame's first axis ("a" = u) with sign sg
+// (+1: molecules with positive a-velocity, -1: negative). Output (mass,
+// a-momentum, b-momentum, energy).
+__device__ __forceinline__ void split_flux_a(const double r, const double ua, const double ub,
+                                             const double p, const double sb, const double sg,
+                                             const double gm1_inv, double g[4]) {
+    const double S = ua * sb;
+    const double A = 0.5 * erfc(-sg * S);
+    const double B = 0.5 * kInvSqrtPi * exp(-S * S) / sb;
+    const double rhoe = p * gm1_inv + 0.5 * r * (ua * ua + ub * ub);
+    const double t = ua * A + sg * B;
+    g[0] = r * t;
+    g[1] = (p + r * ua * ua) * A + sg * r * ua * B;
+    g[2] = r * ub * t;
+    g[3] = (p + rhoe) * ua * A + sg * (rhoe + 0.5 * p) * B;
+}
+
+__device__ __forceinline__ void cons_to_q(const V4& U, const Physics& ph, V4& q, double& rho,
+                                          double& u, double& v, double& p) {
+    rho = U.a;
+    u = U.b / rho;
+    v = U.c / rho;
+    p = ph.gm1 * (U.d - 0.5 * rho * (u * u + v * v));
+    const double beta = rho / (2.0 * p);
+    q.a = log(rho) + log(beta) * ph.gm1_inv - beta * (u * u + v * v);
+    q.b = 2.0 * beta * u;
+    q.c = 2.0 * beta * v;
+    q.d = -2.0 * beta;
+}
+
+__device__ __forceinline__ bool physical(double rho, double u, double v, double p) {
+    return rho > 0.0 && p > 0.0 && isfinite(rho) && isfinite(p) && isfinite(u) && isfinite(v);
+}
+
+// Block-wide sum in a fixed order (warp shuffles, then the warps' partials
+// by the first warp), so the result does not depend on timing.
+template <int BLOCK>
+__device__ __forceinline__ double block_sum(double x) {
+    __shared__ double warp_part[BLOCK / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) warp_part[wid] = x;
+    __syncthreads();
+    double s = 0.0;
+    if (wid == 0) {
+        s = lane < BLOCK / 32 ? warp_part[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    }
+    return s;  // valid in thread 0
+}
+
+// ----------------------------------------------------------- q-derivatives
+
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_ls_first(const DevGeom g, const V4* __restrict__ q,
+                                                    V8* __restrict__ dq) {
+    const int64_t d = int64_t(blockIdx.x) * BLOCK + threadIdx.x;
+    if (d >= g.n) return;
+    const V4 qi = ld4(q + d);
+    double ax[4] = {0, 0, 0, 0}, ay[4] = {0, 0, 0, 0};
+    const int c = g.cnt[d];
+    for (int k = 0; k < c; ++k) {
+        const int64_t at = int64_t(k) * g.stride + d;
+        const uint32_t j = g.nbr[at] & kIndexMask;
+        const double wx = g.wx[at], wy = g.wy[at];
+        const V4 qj = ld4(q + j);
+        const double dq0 = qj.a - qi.a, dq1 = qj.b - qi.b, dq2 = qj.c - qi.c, dq3 = qj.d - qi.d;
+        ax[0] += wx * dq0; ax[1] += wx * dq1; ax[2] += wx * dq2; ax[3] += wx * dq3;
+        ay[0] += wy * dq0; ay[1] += wy * dq1; ay[2] += wy * dq2; ay[3] += wy * dq3;
+    }
+    V8 o;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        o.x[m] = ax[m];
+        o.y[m] = ay[m];
+    }
+    dq[d] = o;
+}
+
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_ls_inner(const DevGeom g, const V4* __restrict__ q,
+                                                    const V8* __restrict__ din,
+                                                    V8* __restrict__ dout) {
+    const int64_t d = int64_t(blockIdx.x) * BLOCK + threadIdx.x;
+    if (d >= g.n) return;
+    const V4 qi = ld4(q + d);
+    const V8 di = din[d];
+    const double qiv[4] = {qi.a, qi.b, qi.c, qi.d};
+    double ax[4] = {0, 0, 0, 0}, ay[4] = {0, 0, 0, 0};
+    const int c = g.cnt[d];
+    for (int k = 0; k < c; ++k) {
+        const int64_t at = int64_t(k) * g.stride + d;
+        const uint32_t j = g.nbr[at] & kIndexMask;
+        const double wx = g.wx[at], wy = g.wy[at];
+        const double hx = g.hdx[at], hy = g.hdy[at];
+        const V4 qj = ld4(q + j);
+        const V8 dj = din[j];
+        const double qjv[4] = {qj.a, qj.b, qj.c, qj.d};
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            // dq~ = q~_j - q~_0 (Eq. 28) with q~ = q - (dx q_x + dy q_y) / 2
+            const double dqt = (qjv[m] - qiv[m]) - (hx * (dj.x[m] - di.x[m]) + hy * (dj.y[m] - di.y[m]));
+            ax[m] += wx * dqt;
+            ay[m] += wy * dqt;
+        }
+    }
+    V8 o;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        o.x[m] = ax[m];
+        o.y[m] = ay[m];
+    }
+    dout[d] = o;
+}
+
+// ------------------------------------------------------- flux residual + RK
+
+template <int MODE, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_flux(const DevGeom g, const Physics ph,
+                                                const DevState st, const V4* __restrict__ q_in,
+                                                const V8* __restrict__ dq, V4* __restrict__ q_out) {
+    const int64_t d = int64_t(blockIdx.x) * BLOCK + threadIdx.x;
+    double r2 = 0.0;
+    if (d < g.n) {
+        const int8_t fl = g.flag[d];
+        const bool fixed = ph.outer_fixed && fl == LSKUM_OUTER;
+        double R[4] = {0.0, 0.0, 0.0, 0.0};
+        if (!fixed) {
+            double tx = 1.0, ty = 0.0, nx = 0.0, ny = 1.0;
+            const bool local = fl != LSKUM_INTERIOR;
+            if (local) {
+                const double2 nn = g.nrm[d];
+                nx = nn.x;
+                ny = nn.y;
+                tx = ny;
+                ty = -nx;
+            }
+            const V4 qi = ld4(q_in + d);
+            const V8 di = dq[d];
+            const double qiv[4] = {qi.a, qi.b, qi.c, qi.d};
+            const bool second = ph.order == 2;
+            const int c = g.cnt[d];
+            for (int k = 0; k < c; ++k) {
+                const int64_t at = int64_t(k) * g.stride + d;
+                const uint32_t e = g.nbr[at];
+                const uint32_t j = e & kIndexMask;
+                const uint32_t sc = (e >> kIndexBits) & 3u;
+                const uint32_t nc = (e >> (kIndexBits + 2)) & 3u;
+                const V4 qj = ld4(q_in + j);
+                double tj[4] = {qj.a, qj.b, qj.c, qj.d};
+                double t0[4] = {qiv[0], qiv[1], qiv[2], qiv[3]};
+                if (second) {
+                    const double hx = g.hdx[at], hy = g.hdy[at];
+                    const V8 dj = dq[j];
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        tj[m] = tj[m] - (hx * dj.x[m] + hy * dj.y[m]);
+                        t0[m] = t0[m] - (hx * di.x[m] + hy * di.y[m]);
+                    }
+                }
+                // equal modified states give dG = 0 exactly (free-stream preservation);
+                // the two inlined flux evaluations below need not round identically
+                if (tj[0] == t0[0] && tj[1] == t0[1] && tj[2] == t0[2] && tj[3] == t0[3]) continue;
+                Prim wj = q_to_prim(tj[0], tj[1], tj[2], tj[3], ph.gm1_inv);
+                Prim w0 = q_to_prim(t0[0], t0[1], t0[2], t0[3], ph.gm1_inv);
+                if (local) {  // velocities into (s, n)
+                    const double sj = wj.u * tx + wj.v * ty, nj = wj.u * nx + wj.v * ny;
+                    const double s0 = w0.u * tx + w0.v * ty, n0 = w0.u * nx + w0.v * ny;
+                    wj.u = sj; wj.v = nj;
+                    w0.u = s0; w0.v = n0;
+                }
+                if (sc) {
+                    const double sg = sc == 1u ? 1.0 : -1.0;
+                    double gj[4], g0[4];
+                    split_flux_a(wj.r, wj.u, wj.v, wj.p, wj.sb, sg, ph.gm1_inv, gj);
+                    split_flux_a(w0.r, w0.u, w0.v, w0.p, w0.sb, sg, ph.gm1_inv, g0);
+                    const double w = g.ws[at];
+                    R[0] += w * (gj[0] - g0[0]);
+                    R[1] += w * (gj[1] - g0[1]);
+                    R[2] += w * (gj[2] - g0[2]);
+                    R[3] += w * (gj[3] - g0[3]);
+                }
+                if (nc) {
+                    const double sg = nc == 1u ? 1.0 : -1.0;
+                    double gj[4], g0[4];
+                    // along n: "a" = n-velocity, "b" = s-velocity
+                    split_flux_a(wj.r, wj.v, wj.u, wj.p, wj.sb, sg, ph.gm1_inv, gj);
+                    split_flux_a(w0.r, w0.v, w0.u, w0.p, w0.sb, sg, ph.gm1_inv, g0);
+                    const double w = g.wn[at];
+                    R[0] += w * (gj[0] - g0[0]);
+                    R[1] += w * (gj[2] - g0[2]);  // s-momentum
+                    R[2] += w * (gj[1] - g0[1]);  // n-momentum
+                    R[3] += w * (gj[3] - g0[3]);
+                }
+            }
+            if (local) {  // momentum back to the global frame
+                const double rs = R[1], rn = R[2];
+                R[1] = rs * tx + rn * nx;
+                R[2] = rs * ty + rn * ny;
+            }
+        }
+        if (MODE == 0) {
+            st.R[d] = V4{R[0], R[1], R[2], R[3]};
+        } else {
+            V4 U = ld4(st.U + d);
+            double dtv;
+            if (MODE == 1) {
+                const double rho = U.a, u = U.b / rho, v = U.c / rho;
+                const double p = ph.gm1 * (U.d - 0.5 * rho * (u * u + v * v));
+                dtv = ph.cfl * g.dmin[d] / (sqrt(u * u + v * v) + sqrt(ph.gamma * p / rho));
+                st.dt[d] = dtv;
+                st.U0[d] = U;
+                r2 = R[0] * R[0];
+            } else {
+                dtv = st.dt[d];
+            }
+            if (!fixed) {
+                const double h = 0.5 * dtv;
+                if (MODE == 3) {
+                    const V4 U0 = ld4(st.U0 + d);
+                    U.a = (2.0 / 3.0) * U0.a + (1.0 / 3.0) * (U.a - h * R[0]);
+                    U.b = (2.0 / 3.0) * U0.b + (1.0 / 3.0) * (U.b - h * R[1]);
+                    U.c = (2.0 / 3.0) * U0.c + (1.0 / 3.0) * (U.c - h * R[2]);
+                    U.d = (2.0 / 3.0) * U0.d + (1.0 / 3.0) * (U.d - h * R[3]);
+                } else {
+                    U.a -= h * R[0];
+                    U.b -= h * R[1];
+                    U.c -= h * R[2];
+                    U.d -= h * R[3];
+                }
+                if (fl == LSKUM_WALL) {  // remove the wall-normal momentum
+                    const double2 nn = g.nrm[d];
+                    const double tx = nn.y, ty = -nn.x;
+                    const double ms = U.b * tx + U.c * ty;
+                    U.b = ms * tx;
+                    U.c = ms * ty;
+                }
+                st.U[d] = U;
+            }
+            V4 qn;
+            double rho, u, v, p;
+            cons_to_q(U, ph, qn, rho, u, v, p);
+            q_out[d] = qn;
+            if (!physical(rho, u, v, p)) atomicOr(st.status, 1);
+        }
+    }
+    if (MODE == 1) {
+        const double s = block_sum<BLOCK>(r2);
+        if (threadIdx.x == 0) st.partials[blockIdx.x] = s;
+    }
+}
+
+// Residue = sqrt(sum of the per-block partials) / N, summed in block order by
+// one block (deterministic), appended to the history ring buffer.
+__global__ void __launch_bounds__(kReduceBlock) k_residue(const DevState st, int nblocks,
+                                                          int64_t n) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += kReduceBlock) s += st.partials[b];
+    s = block_sum<kReduceBlock>(s);
+    if (threadIdx.x == 0) {
+        const unsigned long long it = *st.iter_counter;
+        const double r = sqrt(s) / double(n);
+        st.res_hist[it % (unsigned long long)st.res_cap] = r;
+        *st.iter_counter = it + 1;
+        if (!isfinite(r)) atomicOr(st.status, 1);
+    }
+}
+
+// ------------------------------------------------------------ state I/O
+
+__global__ void k_set_uniform(const DevGeom g, const Physics ph, const V4 W, V4* U, V4* q) {
+    const int64_t d = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (d >= g.n) return;
+    V4 u;
+    u.a = W.a;
+    u.b = W.a * W.b;
+    u.c = W.a * W.c;
+    u.d = W.d * ph.gm1_inv + 0.5 * W.a * (W.b * W.b + W.c * W.c);
+    U[d] = u;
+    V4 qq;
+    double rho, uu, vv, p;
+    cons_to_q(u, ph, qq, rho, uu, vv, p);
+    q[d] = qq;
+}
+
+__global__ void k_set_prim(const DevGeom g, const Physics ph, const V4* __restrict__ W_user,
+                           V4* U, V4* q, int* status) {
+    const int64_t d = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (d >= g.n) return;
+    const V4 W = W_user[g.dev_to_user[d]];
+    if (!physical(W.a, W.b, W.c, W.d)) atomicOr(status, 2);
+    V4 u;
+    u.a = W.a;
+    u.b = W.a * W.b;
+    u.c = W.a * W.c;
+    u.d = W.d * ph.gm1_inv + 0.5 * W.a * (W.b * W.b + W.c * W.c);
+    U[d] = u;
+    V4 qq;
+    double rho, uu, vv, p;
+    cons_to_q(u, ph, qq, rho, uu, vv, p);
+    q[d] = qq;
+}
+
+__global__ void k_get_prim(const DevGeom g, const Physics ph, const V4* __restrict__ U,
+                           V4* __restrict__ W_user) {
+    const int64_t d = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (d >= g.n) return;
+    const V4 u = U[d];
+    const double rho = u.a, uu = u.b / rho, vv = u.c / rho;
+    const double p = ph.gm1 * (u.d - 0.5 * rho * (uu * uu + vv * vv));
+    W_user[g.dev_to_user[d]] = V4{rho, uu, vv, p};
+}
+
+template <typename T>
+__global__ void k_gather(const DevGeom g, const T* __restrict__ src, T* __restrict__ dst) {
+    const int64_t d = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (d >= g.n) return;
+    dst[g.dev_to_user[d]] = src[d];
+}
+
+// Pressure force on the wall loops: F = -sum (p_i - p_inf) n_i ds_i.
+__global__ void __launch_bounds__(kReduceBlock) k_forces(const DevGeom g, const Physics ph,
+                                                         const DevState st) {
+    double fx = 0.0, fy = 0.0;
+    for (int64_t k = threadIdx.x; k < g.n_wall; k += kReduceBlock) {
+        const int32_t d = g.wall_id[k];
+        const V4 u = st.U[d];
+        const double rho = u.a, uu = u.b / rho, vv = u.c / rho;
+        const double p = ph.gm1 * (u.d - 0.5 * rho * (uu * uu + vv * vv));
+        const double2 nds = g.wall_nds[k];
+        fx -= (p - ph.p_inf) * nds.x;
+        fy -= (p - ph.p_inf) * nds.y;
+    }
+    fx = block_sum<kReduceBlock>(fx);
+    __syncthreads();
+    fy = block_sum<kReduceBlock>(fy);
+    if (threadIdx.x == 0) {
+        st.force_out[0] = fx;
+        st.force_out[1] = fy;
+    }
+}
+
+inline unsigned grid_for(int64_t n, int block) { return unsigned((n + block - 1) / block); }
+
+}  // namespace
+
+cudaError_t launch_ls_first(const DevGeom& g, const V4* q, V8* dq, int block, cudaStream_t s) {
+    if (block == 256)
+        k_ls_first<256><<<grid_for(g.n, 256), 256, 0, s>>>(g, q, dq);
+    else
+        k_ls_first<kDefaultBlock><<<grid_for(g.n, kDefaultBlock), kDefaultBlock, 0, s>>>(g, q, dq);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ls_inner(const DevGeom& g, const V4* q, const V8* din, V8* dout, int block,
+                            cudaStream_t s) {
+    if (block == 256)
+        k_ls_inner<256><<<grid_for(g.n, 256), 256, 0, s>>>(g, q, din, dout);
+    else
+        k_ls_inner<kDefaultBlock><<<grid_for(g.n, kDefaultBlock), kDefaultBlock, 0, s>>>(g, q, din, dout);
+    return cudaGetLastError();
+}
+
+template <int BLOCK>
+static void flux_dispatch(int mode, const DevGeom& g, const Physics& ph, const DevState& st,
+                          const V4* q_in, const V8* dq, V4* q_out, cudaStream_t s) {
+    const unsigned grid = grid_for(g.n, BLOCK);
+    switch (mode) {
+        case 0: k_flux<0, BLOCK><<<grid, BLOCK, 0, s>>>(g, ph, st, q_in, dq, q_out); break;
+        case 1: k_flux<1, BLOCK><<<grid, BLOCK, 0, s>>>(g, ph, st, q_in, dq, q_out); break;
+        case 2: k_flux<2, BLOCK><<<grid, BLOCK, 0, s>>>(g, ph, st, q_in, dq, q_out); break;
+        case 3: k_flux<3, BLOCK><<<grid, BLOCK, 0, s>>>(g, ph, st, q_in, dq, q_out); break;
+        default: k_flux<4, BLOCK><<<grid, BLOCK, 0, s>>>(g, ph, st, q_in, dq, q_out); break;
+    }
+}
+
+cudaError_t launch_flux(int mode, const DevGeom& g, const Physics& ph, const DevState& st,
+                        const V4* q_in, const V8* dq, V4* q_out, int block, cudaStream_t s) {
+    if (block == 256)
+        flux_dispatch<256>(mode, g, ph, st, q_in, dq, q_out, s);
+    else
+        flux_dispatch<kDefaultBlock>(mode, g, ph, st, q_in, dq, q_out, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residue(const DevState& st, int nblocks, int64_t n, cudaStream_t s) {
+    k_residue<<<1, kReduceBlock, 0, s>>>(st, nblocks, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_uniform(const DevGeom& g, const Physics& ph, V4 W, V4* U, V4* q,
+                               cudaStream_t s) {
+    k_set_uniform<<<grid_for(g.n, 256), 256, 0, s>>>(g, ph, W, U, q);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_prim(const DevGeom& g, const Physics& ph, const V4* W_user, V4* U, V4* q,
+                            int* status, cudaStream_t s) {
+    k_set_prim<<<grid_for(g.n, 256), 256, 0, s>>>(g, ph, W_user, U, q, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_get_prim(const DevGeom& g, const Physics& ph, const V4* U, V4* W_user,
+                            cudaStream_t s) {
+    k_get_prim<<<grid_for(g.n, 256), 256, 0, s>>>(g, ph, U, W_user);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_v4(const DevGeom& g, const V4* src, V4* dst, cudaStream_t s) {
+    k_gather<V4><<<grid_for(g.n, 256), 256, 0, s>>>(g, src, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_v8(const DevGeom& g, const V8* src, V8* dst, cudaStream_t s) {
+    k_gather<V8><<<grid_for(g.n, 256), 256, 0, s>>>(g, src, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_forces(const DevGeom& g, const Physics& ph, const DevState& st, cudaStream_t s) {
+    k_forces<<<1, kReduceBlock, 0, s>>>(g, ph, st);
+    return cudaGetLastError();
+}
+
+}  // namespace lskum

@@ -1,0 +1,95 @@
+// Device data layout and kernel launchers of the q-LSKUM solver.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace lskum {
+
+// 4-vector per point (primitive, conserved or q-variables), 32-byte aligned
+// so one record is one DRAM sector.
+struct __align__(32) V4 {
+    double a, b, c, d;
+};
+
+// q-derivatives of one point: (q_x[4], q_y[4]), 64-byte aligned.
+struct __align__(64) V8 {
+    double x[4];
+    double y[4];
+};
+
+// Static cloud data on the device (device point order).
+struct DevGeom {
+    int64_t n;
+    int64_t stride;  // row length of the slot-major arrays
+    int slots;
+    const int32_t* cnt;
+    const int8_t* flag;
+    const double2* nrm;
+    const double* dmin;
+    const uint32_t* nbr;  // [slot][stride] packed entries (lskum_internal.h)
+    const double* hdx;
+    const double* hdy;
+    const double* wx;
+    const double* wy;
+    const double* ws;
+    const double* wn;
+    const int32_t* dev_to_user;
+    const int32_t* user_to_dev;
+    int64_t n_wall;
+    const int32_t* wall_id;
+    const double2* wall_nds;
+};
+
+struct Physics {
+    double gamma;
+    double gm1;      // gamma - 1
+    double gm1_inv;  // 1 / (gamma - 1)
+    double cfl;
+    double p_inf;
+    int order;        // 1 or 2
+    int outer_fixed;  // far-field points hold the free stream
+};
+
+// Mutable solver state (device order).
+struct DevState {
+    V4* U;     // conserved state
+    V4* U0;    // state at the start of the iteration
+    V4* q[2];  // q-variables, double-buffered across stages
+    V8* dq[2]; // q-derivatives, double-buffered across inner iterations
+    double* dt;
+    V4* R;     // residual output of the evaluation mode
+    double* partials;  // per-block partial sums (scratch)
+    double* res_hist;  // residue per iteration (ring buffer)
+    int64_t res_cap;
+    unsigned long long* iter_counter;
+    int* status;       // bit 0: non-physical state seen
+    double* force_out; // (Fx, Fy)
+};
+
+constexpr int kDefaultBlock = 128;
+constexpr int kReduceBlock = 512;
+
+enum KernelClass { kFlux = 0, kLsFirst = 1, kLsInner = 2, kReduce = 3, kNumKernelClasses = 4 };
+
+// Launchers (return cudaGetLastError()).
+cudaError_t launch_ls_first(const DevGeom& g, const V4* q, V8* dq, int block, cudaStream_t s);
+cudaError_t launch_ls_inner(const DevGeom& g, const V4* q, const V8* dq_in, V8* dq_out, int block,
+                            cudaStream_t s);
+// mode 0: evaluate R only (written to st.R); mode 1..4: SSP-RK stage.
+cudaError_t launch_flux(int mode, const DevGeom& g, const Physics& ph, const DevState& st,
+                        const V4* q_in, const V8* dq, V4* q_out, int block, cudaStream_t s);
+cudaError_t launch_residue(const DevState& st, int nblocks, int64_t n, cudaStream_t s);
+cudaError_t launch_set_uniform(const DevGeom& g, const Physics& ph, V4 W, V4* U, V4* q,
+                               cudaStream_t s);
+cudaError_t launch_set_prim(const DevGeom& g, const Physics& ph, const V4* W_user, V4* U, V4* q,
+                            int* status, cudaStream_t s);
+cudaError_t launch_get_prim(const DevGeom& g, const Physics& ph, const V4* U, V4* W_user,
+                            cudaStream_t s);
+cudaError_t launch_gather_v4(const DevGeom& g, const V4* src_dev, V4* dst_user, cudaStream_t s);
+cudaError_t launch_gather_v8(const DevGeom& g, const V8* src_dev, V8* dst_user, cudaStream_t s);
+cudaError_t launch_forces(const DevGeom& g, const Physics& ph, const DevState& st,
+                          cudaStream_t s);
+
+}  // namespace lskum

@@ -1,0 +1,251 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerances: FP64 path within 1e-12 relative (norm-wise per component) on one
+residual evaluation / one iteration, and within 1e-9 on the state after 1000
+iterations. Norm-wise because the split-flux differences G(q~_j) - G(q~_0)
+cancel and amplify the last-ulp differences of libm and CUDA erfc/exp/log at
+individual points.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2108_07031_gb300 import cloud as Cl
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2108_07031_gb300 import lskum as L  # noqa: E402
+
+TOL_ONE_STEP = 1e-12
+TOL_1000 = 1e-9
+
+
+def normwise(a, b):
+    """max over components of max_i |a - b| / max_i |b|."""
+    a = np.asarray(a)
+    b = np.asarray(b)
+    scale = np.abs(b).max(axis=0)
+    scale = np.where(scale > 0, scale, 1.0)
+    return float((np.abs(a - b).max(axis=0) / scale).max())
+
+
+@pytest.fixture(scope="module")
+def c5k():
+    return Cl.naca0012_cloud(128, 40)
+
+
+@pytest.fixture(scope="module")
+def c_ragged():
+    # 130 x 41 = 5330 points: not a multiple of the 128-thread block, shuffled input
+    return Cl.naca0012_cloud(130, 41, shuffle=True, seed=99)
+
+
+def oracle_for(cloud, **kw):
+    return O.OracleCloud.from_cloud(cloud, **kw)
+
+
+def test_set_get_state_roundtrip(c_ragged):
+    W = Cl.perturbed_state(c_ragged, 0.63, 2.0)
+    with L.Solver.from_cloud(c_ragged) as s:
+        s.set_state(W)
+        assert np.array_equal(s.get_state(), W) or normwise(s.get_state(), W) < 1e-15
+        info = s.info()
+        assert info["n_points"] == c_ragged.n and info["n_wall"] == c_ragged.n_c
+
+
+@pytest.mark.parametrize("inner", [0, 2, 3])
+def test_q_derivatives_parity(c_ragged, inner):
+    W = Cl.perturbed_state(c_ragged, 0.63, 2.0)
+    oc = oracle_for(c_ragged)
+    qx_o, qy_o = O.q_derivatives(oc, O.prim_to_q(W), inner)
+    with L.Solver.from_cloud(c_ragged, inner_iters=inner) as s:
+        s.set_state(W)
+        qx, qy = s.eval_q_derivatives()
+    assert normwise(qx, qx_o) < TOL_ONE_STEP
+    assert normwise(qy, qy_o) < TOL_ONE_STEP
+
+
+@pytest.mark.parametrize("which", ["c5k", "c_ragged"])
+def test_residual_parity_perturbed_state(which, request):
+    cloud = request.getfixturevalue(which)
+    W = Cl.perturbed_state(cloud, 0.63, 2.0)
+    R_o, bad = O.residual_of_state(oracle_for(cloud), W, inner=2)
+    assert bad == 0
+    with L.Solver.from_cloud(cloud) as s:
+        s.set_state(W)
+        R = s.eval_residual()
+    assert normwise(R, R_o) < TOL_ONE_STEP
+    # elementwise: the norm-wise bound plus a relative slack per element
+    scale = np.abs(R_o).max(axis=0, keepdims=True)
+    err = np.abs(R - R_o)
+    assert np.all(err <= TOL_ONE_STEP * scale + 1e-10 * np.abs(R_o)), err.max(0) / scale
+
+
+def test_uniform_state_has_exactly_zero_residual(c_ragged):
+    with L.Solver.from_cloud(c_ragged) as s:
+        for mach, alpha in ((0.63, 2.0), (0.85, 1.0)):
+            s.set_freestream(mach, alpha)
+            R = s.eval_residual()
+            assert np.all(R == 0.0)
+
+
+def test_residual_parity_after_50_oracle_iterations(c5k):
+    """The survey's one-step case: the oracle's state after 50 iterations from
+    the free stream, injected with set_state, then one residual evaluation."""
+    oc = oracle_for(c5k)
+    W0 = np.tile(O.freestream(0.63, 2.0), (c5k.n, 1))
+    W50, res, st = O.iterate(oc, W0, 50)
+    assert st == 0
+    R_o, _ = O.residual_of_state(oc, W50, inner=2)
+    with L.Solver.from_cloud(c5k) as s:
+        s.set_state(W50)
+        R = s.eval_residual()
+    assert normwise(R, R_o) < TOL_ONE_STEP
+
+
+def test_one_iteration_parity(c_ragged):
+    W = Cl.perturbed_state(c_ragged, 0.63, 2.0)
+    oc = oracle_for(c_ragged)
+    W1, res_o, st = O.iterate(oc, W, 1)
+    assert st == 0
+    with L.Solver.from_cloud(c_ragged) as s:
+        s.set_state(W)
+        s.step(1)
+        W1g = s.get_state()
+        r = s.residual_norm()
+    assert normwise(W1g, W1) < TOL_ONE_STEP
+    assert abs(r - res_o[0]) <= TOL_ONE_STEP * res_o[0]
+
+
+def test_1000_iterations_parity(c5k):
+    """State after 1000 iterations from the free stream (M 0.63, alpha 2 deg)."""
+    oc = oracle_for(c5k)
+    W0 = np.tile(O.freestream(0.63, 2.0), (c5k.n, 1))
+    W_o, res_o, st = O.iterate(oc, W0, 1000)
+    assert st == 0
+    with L.Solver.from_cloud(c5k) as s:
+        s.set_freestream(0.63, 2.0)
+        hist = []
+        for _ in range(10):
+            s.step(100)
+            hist.append(s.residual_norm())
+        W = s.get_state()
+        cl, cd = s.forces()
+    assert normwise(W, W_o) < TOL_1000
+    ref = res_o[99::100]
+    assert np.all(np.abs(np.array(hist) - ref) <= TOL_1000 * ref)
+    cl_o, cd_o = O.forces(oc, W_o, c5k.wall_loop, 0.63, 2.0)
+    assert abs(cl - cl_o) < 1e-9 and abs(cd - cd_o) < 1e-9
+
+
+@pytest.mark.parametrize("opts", [
+    dict(order=1, inner_iters=0),
+    dict(inner_iters=0),
+    dict(inner_iters=3),
+    dict(outer_mode=0),
+    dict(block_size=256),
+    dict(reorder=0),
+    dict(wall_factor=1.0),
+])
+def test_option_variants_parity(c_ragged, opts):
+    ok = {k: v for k, v in opts.items() if k in ("order", "wall_factor", "outer_mode")}
+    oc = oracle_for(c_ragged, **ok)
+    W = Cl.perturbed_state(c_ragged, 0.85, 1.0)
+    inner = opts.get("inner_iters", 2)
+    R_o, _ = O.residual_of_state(oc, W, inner=inner)
+    W3, _, st = O.iterate(oc, W, 3, inner=inner)
+    assert st == 0
+    with L.Solver.from_cloud(c_ragged, **opts) as s:
+        s.set_state(W)
+        R = s.eval_residual()
+        s.step(3)
+        W3g = s.get_state()
+    assert normwise(R, R_o) < TOL_ONE_STEP
+    assert normwise(W3g, W3) < 1e-11
+
+
+def test_tiny_cloud_less_than_two_blocks():
+    c = Cl.naca0012_cloud(24, 8)  # 192 points: one full and one ragged block
+    oc = oracle_for(c)
+    W = Cl.perturbed_state(c, 0.5, 3.0)
+    W5, res, st = O.iterate(oc, W, 5)
+    with L.Solver.from_cloud(c) as s:
+        s.set_state(W)
+        s.step(5)
+        assert normwise(s.get_state(), W5) < 1e-11
+
+
+def test_graph_and_plain_launches_agree_bitwise(c5k):
+    """Replaying the captured iteration graph and issuing plain launches (the
+    profiling path) give bit-identical states: the reductions are ordered."""
+    with L.Solver.from_cloud(c5k) as s:
+        s.set_freestream(0.63, 2.0)
+        s.step(20)
+        Wa = s.get_state()
+        s.set_freestream(0.63, 2.0)
+        s.profile(True)
+        s.step(20)
+        s.profile(False)
+        Wb = s.get_state()
+        ms, n = s.kernel_time(L.KERNEL_FLUX)
+        assert n == 80 and ms > 0
+        ms2, n2 = s.kernel_time(L.KERNEL_LS_INNER)
+        assert n2 == 160
+    assert np.array_equal(Wa, Wb)
+
+
+def test_solve_reaches_tolerance_or_budget(c5k):
+    with L.Solver.from_cloud(c5k, check_every=25) as s:
+        s.set_freestream(0.63, 2.0)
+        done = s.solve(400, 1e-1)
+        r = s.residual_norm()
+        assert 0 < done <= 400
+        assert r > 0
+
+
+def test_divergence_is_reported_not_faulted(c_ragged):
+    with L.Solver.from_cloud(c_ragged) as s:
+        bad = Cl.perturbed_state(c_ragged, 0.63, 2.0)
+        bad[17, 0] = -1.0
+        with pytest.raises(L.LskumError) as e:
+            s.set_state(bad)
+        assert e.value.code == -5
+        wild = Cl.perturbed_state(c_ragged, 0.63, 2.0, amplitude=0.0)
+        wild[::7, 3] = 1e-6   # near-vacuum pressure pockets next to p ~ 0.7
+        wild[::11, 1] = 25.0  # and strong velocity jumps
+        s.set_state(wild)
+        with pytest.raises(L.LskumError) as e:
+            s.step(20)
+        assert e.value.code == -5
+        # the context stays usable
+        s.set_freestream(0.63, 2.0)
+        s.step(2)
+        assert np.isfinite(s.residual_norm())
+
+
+def test_full_size_residual_parity_sampled():
+    """10M-point cloud (5658 x 1768, shuffled input), the launch configuration
+    of the benchmark: q-derivatives and residual at 2000 sampled points."""
+    n_c, n_r = Cl.cloud_dims(10_000_000)
+    c = Cl.naca0012_cloud(n_c, n_r, shuffle=True)
+    W = Cl.perturbed_state(c, 0.63, 2.0)
+    with L.Solver.from_cloud(c) as s:
+        s.set_state(W)
+        R = s.eval_residual()
+        qx, qy = s.eval_q_derivatives()
+    oc = oracle_for(c)
+    q = O.prim_to_q(W)
+    qx_o, qy_o = O.q_derivatives(oc, q, 2)
+    rng = np.random.Generator(np.random.PCG64(4))
+    idx = np.concatenate([np.arange(n_c), rng.choice(c.n, 2000, replace=False),
+                          np.nonzero(c.flags == 2)[0][:200]])
+    R_o, bad = O.flux_residual_subset(oc, q, qx_o, qy_o, idx)
+    assert bad == 0
+    assert normwise(qx[idx], qx_o[idx]) < TOL_ONE_STEP
+    assert normwise(qy[idx], qy_o[idx]) < TOL_ONE_STEP
+    assert normwise(R[idx], R_o) < TOL_ONE_STEP
