@@ -168,6 +168,32 @@ int lskum_kernel_time(lskum_ctx* ctx, int kernel, double* total_ms, int64_t* lau
 /* Number of kernel launches issued by the last lskum_step call. */
 int64_t lskum_last_launch_count(lskum_ctx* ctx);
 
+/*
+ * Residue of a residual the caller already holds, computed without allocating
+ * any memory. The paper has no counterpart: this exists for callers that may
+ * not allocate device memory at all (code running inside a CUDA-graph capture
+ * it does not own, plug-ins whose host framework owns every device allocation,
+ * runtimes that forbid allocation after start-up).
+ *   R       DEVICE pointer to n x 4 residual values (row-major per point, as
+ *           returned by lskum_eval_residual); only R[4 i] (mass) is read
+ *   n       number of points, 1 <= n <= LSKUM_NOALLOC_MAX_POINTS
+ *   out     DEVICE pointer to one double: sqrt(sum_i R[4 i]^2) / n
+ *   stream  cudaStream_t to run on (NULL: the legacy default stream)
+ * The kernels keep their per-block partial sums in one fixed 64 KiB array
+ * inside the library (8192 partials of 8192 points each); every GPU that
+ * loads the library holds that array until the process exits. The first call
+ * on each device looks the array's device address up (no allocation); make
+ * that first call before any stream capture. All calls on a device share the
+ * array and each call overwrites the part it reads, so nothing carries over
+ * between calls, but calls that overlap on the GPU (different streams, no
+ * ordering between them) race on it. Asynchronous: *out is ready when the
+ * stream reaches the end of the call.
+ * Errors: INVALID_ARG (null pointer, n out of range; nothing is launched),
+ * CUDA (device query or launch failed).
+ */
+#define LSKUM_NOALLOC_MAX_POINTS (8192LL * 8192LL)
+int lskum_residue_noalloc(const double* R, int64_t n, double* out, void* stream);
+
 /* Human-readable name of a return code (static storage). */
 const char* lskum_error_string(int code);
 

@@ -35,8 +35,10 @@ EXPORTED = (
     "lskum_set_freestream", "lskum_set_state", "lskum_get_state", "lskum_step", "lskum_solve",
     "lskum_residual_norm", "lskum_forces", "lskum_eval_residual", "lskum_eval_q_derivatives",
     "lskum_info", "lskum_profile", "lskum_kernel_time", "lskum_last_launch_count",
-    "lskum_error_string", "lskum_last_error",
+    "lskum_error_string", "lskum_last_error", "lskum_residue_noalloc",
 )
+
+NOALLOC_MAX_POINTS = 8192 * 8192
 
 
 class LskumError(RuntimeError):
@@ -89,6 +91,7 @@ def load(build_if_missing: bool = True):
             "lskum_last_launch_count": ([P], I64),
             "lskum_error_string": ([I], C.c_char_p),
             "lskum_last_error": ([], C.c_char_p),
+            "lskum_residue_noalloc": ([P, I64, P, P], I),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -124,6 +127,15 @@ def _host_f64(a, shape):
     if a.shape != shape:
         a = a.reshape(shape)
     return a
+
+
+def residue_noalloc(R_device_ptr: int, n: int, out_device_ptr: int, stream_handle: int = 0):
+    """``lskum_residue_noalloc``: residue sqrt(sum R_rho^2) / n of a device-resident
+    n x 4 residual into one device double, with no allocation (fixed scratch)."""
+    lib = load()
+    _check(lib.lskum_residue_noalloc(C.c_void_p(R_device_ptr), int(n),
+                                     C.c_void_p(out_device_ptr), C.c_void_p(stream_handle)),
+           "lskum_residue_noalloc")
 
 
 class Solver:
