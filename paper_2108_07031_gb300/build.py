@@ -22,7 +22,7 @@ PROBE = os.path.join(BUILD, "pipe_peaks")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CUDA_SOURCES = ["lskum_kernels.cu", "lskum_api.cu", "lskum_noalloc.cu"]
 HOST_SOURCES = ["lskum_setup.cpp"]
-HEADERS = ["lskum_internal.h", "lskum_kernels.cuh"]
+HEADERS = ["lskum_internal.h", "lskum_kernels.cuh", "erfc_tables.h"]
 
 
 def _nvcc() -> str:

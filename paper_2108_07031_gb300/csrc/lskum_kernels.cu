@@ -25,6 +25,7 @@
 #include <cmath>
 
 #include "lskum_internal.h"
+#include "erfc_tables.h"
 #include "lskum_kernels.cuh"
 
 namespace lskum {
@@ -36,10 +37,14 @@ constexpr double kInvSqrtPi = 0.56418958354775628695;  // 1 / sqrt(pi)
 __device__ __forceinline__ V4 ld4(const V4* p) { return *p; }
 
 struct Prim {
-    double r, u, v, p, beta, sb;  // density, velocity (frame components), pressure, beta, sqrt(beta)
+    double r, u, v, p, sb, isb;  // density, velocity (frame components), pressure, sqrt(beta), 1/sqrt(beta)
 };
 
-// q -> primitive (inverse of Eq. 26); velocities in the global frame.
+// q -> primitive (inverse of Eq. 26); velocities in the global frame. With
+// gamma = 1.4 (1/(gamma-1) = 5/2) the factor beta^(-1/(gamma-1)) of the
+// density is (1/sqrt(beta))^5, so no logarithm is needed; 1/sqrt(beta) is
+// needed by the split fluxes anyway.
+template <bool G14>
 __device__ __forceinline__ Prim q_to_prim(const double t0, const double t1, const double t2,
                                           const double t3, const double gm1_inv) {
     Prim w;
@@ -47,22 +52,57 @@ __device__ __forceinline__ Prim q_to_prim(const double t0, const double t1, cons
     const double inv2b = -1.0 / t3;  // 1 / (2 beta)
     w.u = t1 * inv2b;
     w.v = t2 * inv2b;
-    w.r = exp(t0 - log(beta) * gm1_inv + beta * (w.u * w.u + w.v * w.v));
+    w.isb = rsqrt(beta);
+    w.sb = beta * w.isb;
+    const double uu = w.u * w.u + w.v * w.v;
+    if (G14) {
+        const double i2 = w.isb * w.isb;
+        w.r = exp(t0 + beta * uu) * (i2 * i2 * w.isb);
+    } else {
+        w.r = exp(t0 - log(beta) * gm1_inv + beta * uu);
+    }
     w.p = w.r * inv2b;
-    w.beta = beta;
-    w.sb = sqrt(beta);
     return w;
+}
+
+// erfc(x) / 2 given e = exp(-x^2): erf(x) = x P(x^2) for |x| <= 0.5, and
+// erfc(|x|) = e erfcx(|x|) on [0.5, 6] from the piecewise polynomials of
+// erfc_tables.h (the exponential is shared with the split flux's B term);
+// beyond 6 the library erfc (where erfc < 2e-17).
+__device__ __forceinline__ double half_erfc(const double x, const double e) {
+    const double a = fabs(x);
+    if (a <= 0.5) {
+        const double t = x * x;
+        double pv = kErfP[kErfDeg];
+#pragma unroll
+        for (int k = kErfDeg - 1; k >= 0; --k) pv = fma(pv, t, kErfP[k]);
+        return 0.5 - 0.5 * (x * pv);
+    }
+    double ec;
+    if (a <= kErfcxHi) {
+        const int k = min(int((a - kErfcxLo) * kErfcxInvW), kErfcxPieces - 1);
+        const double* c = kErfcxC[k];
+        const double z = a - __ldg(c);
+        double pv = __ldg(c + 1 + kErfcxDeg);
+#pragma unroll
+        for (int m = kErfcxDeg - 1; m >= 0; --m) pv = fma(pv, z, __ldg(c + 1 + m));
+        ec = e * pv;
+    } else {
+        ec = erfc(a);
+    }
+    return x > 0.0 ? 0.5 * ec : 1.0 - 0.5 * ec;
 }
 
 // Kinetic split flux along the frame's first axis ("a" = u) with sign sg
 // (+1: molecules with positive a-velocity, -1: negative). Output (mass,
 // a-momentum, b-momentum, energy).
 __device__ __forceinline__ void split_flux_a(const double r, const double ua, const double ub,
-                                             const double p, const double sb, const double sg,
-                                             const double gm1_inv, double g[4]) {
+                                             const double p, const double sb, const double isb,
+                                             const double sg, const double gm1_inv, double g[4]) {
     const double S = ua * sb;
-    const double A = 0.5 * erfc(-sg * S);
-    const double B = 0.5 * kInvSqrtPi * exp(-S * S) / sb;
+    const double e = exp(-S * S);
+    const double A = half_erfc(-sg * S, e);
+    const double B = (0.5 * kInvSqrtPi) * e * isb;
     const double rhoe = p * gm1_inv + 0.5 * r * (ua * ua + ub * ub);
     const double t = ua * A + sg * B;
     g[0] = r * t;
@@ -173,7 +213,7 @@ __global__ void __launch_bounds__(BLOCK) k_ls_inner(const DevGeom g, const V4* _
 
 // ------------------------------------------------------- flux residual + RK
 
-template <int MODE, int BLOCK>
+template <int MODE, int BLOCK, bool G14>
 __global__ void __launch_bounds__(BLOCK) k_flux(const DevGeom g, const Physics ph,
                                                 const DevState st, const V4* __restrict__ q_in,
                                                 const V8* __restrict__ dq, V4* __restrict__ q_out) {
@@ -219,8 +259,8 @@ __global__ void __launch_bounds__(BLOCK) k_flux(const DevGeom g, const Physics p
                 // equal modified states give dG = 0 exactly (free-stream preservation);
                 // the two inlined flux evaluations below need not round identically
                 if (tj[0] == t0[0] && tj[1] == t0[1] && tj[2] == t0[2] && tj[3] == t0[3]) continue;
-                Prim wj = q_to_prim(tj[0], tj[1], tj[2], tj[3], ph.gm1_inv);
-                Prim w0 = q_to_prim(t0[0], t0[1], t0[2], t0[3], ph.gm1_inv);
+                Prim wj = q_to_prim<G14>(tj[0], tj[1], tj[2], tj[3], ph.gm1_inv);
+                Prim w0 = q_to_prim<G14>(t0[0], t0[1], t0[2], t0[3], ph.gm1_inv);
                 if (local) {  // velocities into (s, n)
                     const double sj = wj.u * tx + wj.v * ty, nj = wj.u * nx + wj.v * ny;
                     const double s0 = w0.u * tx + w0.v * ty, n0 = w0.u * nx + w0.v * ny;
@@ -230,8 +270,8 @@ __global__ void __launch_bounds__(BLOCK) k_flux(const DevGeom g, const Physics p
                 if (sc) {
                     const double sg = sc == 1u ? 1.0 : -1.0;
                     double gj[4], g0[4];
-                    split_flux_a(wj.r, wj.u, wj.v, wj.p, wj.sb, sg, ph.gm1_inv, gj);
-                    split_flux_a(w0.r, w0.u, w0.v, w0.p, w0.sb, sg, ph.gm1_inv, g0);
+                    split_flux_a(wj.r, wj.u, wj.v, wj.p, wj.sb, wj.isb, sg, ph.gm1_inv, gj);
+                    split_flux_a(w0.r, w0.u, w0.v, w0.p, w0.sb, w0.isb, sg, ph.gm1_inv, g0);
                     const double w = g.ws[at];
                     R[0] += w * (gj[0] - g0[0]);
                     R[1] += w * (gj[1] - g0[1]);
@@ -242,8 +282,8 @@ __global__ void __launch_bounds__(BLOCK) k_flux(const DevGeom g, const Physics p
                     const double sg = nc == 1u ? 1.0 : -1.0;
                     double gj[4], g0[4];
                     // along n: "a" = n-velocity, "b" = s-velocity
-                    split_flux_a(wj.r, wj.v, wj.u, wj.p, wj.sb, sg, ph.gm1_inv, gj);
-                    split_flux_a(w0.r, w0.v, w0.u, w0.p, w0.sb, sg, ph.gm1_inv, g0);
+                    split_flux_a(wj.r, wj.v, wj.u, wj.p, wj.sb, wj.isb, sg, ph.gm1_inv, gj);
+                    split_flux_a(w0.r, w0.v, w0.u, w0.p, w0.sb, w0.isb, sg, ph.gm1_inv, g0);
                     const double w = g.wn[at];
                     R[0] += w * (gj[0] - g0[0]);
                     R[1] += w * (gj[2] - g0[2]);  // s-momentum
@@ -419,25 +459,30 @@ cudaError_t launch_ls_inner(const DevGeom& g, const V4* q, const V8* din, V8* do
     return cudaGetLastError();
 }
 
-template <int BLOCK>
+template <int BLOCK, bool G14>
 static void flux_dispatch(int mode, const DevGeom& g, const Physics& ph, const DevState& st,
                           const V4* q_in, const V8* dq, V4* q_out, cudaStream_t s) {
     const unsigned grid = grid_for(g.n, BLOCK);
     switch (mode) {
-        case 0: k_flux<0, BLOCK><<<grid, BLOCK, 0, s>>>(g, ph, st, q_in, dq, q_out); break;
-        case 1: k_flux<1, BLOCK><<<grid, BLOCK, 0, s>>>(g, ph, st, q_in, dq, q_out); break;
-        case 2: k_flux<2, BLOCK><<<grid, BLOCK, 0, s>>>(g, ph, st, q_in, dq, q_out); break;
-        case 3: k_flux<3, BLOCK><<<grid, BLOCK, 0, s>>>(g, ph, st, q_in, dq, q_out); break;
-        default: k_flux<4, BLOCK><<<grid, BLOCK, 0, s>>>(g, ph, st, q_in, dq, q_out); break;
+        case 0: k_flux<0, BLOCK, G14><<<grid, BLOCK, 0, s>>>(g, ph, st, q_in, dq, q_out); break;
+        case 1: k_flux<1, BLOCK, G14><<<grid, BLOCK, 0, s>>>(g, ph, st, q_in, dq, q_out); break;
+        case 2: k_flux<2, BLOCK, G14><<<grid, BLOCK, 0, s>>>(g, ph, st, q_in, dq, q_out); break;
+        case 3: k_flux<3, BLOCK, G14><<<grid, BLOCK, 0, s>>>(g, ph, st, q_in, dq, q_out); break;
+        default: k_flux<4, BLOCK, G14><<<grid, BLOCK, 0, s>>>(g, ph, st, q_in, dq, q_out); break;
     }
 }
 
 cudaError_t launch_flux(int mode, const DevGeom& g, const Physics& ph, const DevState& st,
                         const V4* q_in, const V8* dq, V4* q_out, int block, cudaStream_t s) {
-    if (block == 256)
-        flux_dispatch<256>(mode, g, ph, st, q_in, dq, q_out, s);
-    else
-        flux_dispatch<kDefaultBlock>(mode, g, ph, st, q_in, dq, q_out, s);
+    // gamma = 1.4: log-free density (see q_to_prim)
+    const bool g14 = fabs(ph.gm1_inv - 2.5) < 1e-12;
+    if (block == 256) {
+        if (g14) flux_dispatch<256, true>(mode, g, ph, st, q_in, dq, q_out, s);
+        else flux_dispatch<256, false>(mode, g, ph, st, q_in, dq, q_out, s);
+    } else {
+        if (g14) flux_dispatch<kDefaultBlock, true>(mode, g, ph, st, q_in, dq, q_out, s);
+        else flux_dispatch<kDefaultBlock, false>(mode, g, ph, st, q_in, dq, q_out, s);
+    }
     return cudaGetLastError();
 }
 

@@ -230,7 +230,15 @@ def test_divergence_is_reported_not_faulted(c_ragged):
 
 def test_full_size_residual_parity_sampled():
     """10M-point cloud (5658 x 1768, shuffled input), the launch configuration
-    of the benchmark: q-derivatives and residual at 2000 sampled points."""
+    of the benchmark: q-derivatives and residual at ~7900 sampled points.
+
+    At this resolution the differences q_j - q_i cancel about four digits
+    (|q| / |q_j - q_i| ~ 1e4 with spacings ~5e-4), so any two correct FP64
+    evaluations differ by more than 1e-12. The bound is the problem's own
+    conditioning, measured with the oracle alone: its spread when the state
+    is perturbed by one ulp (random sign per entry), times 8, and never
+    tighter than 1e-12.
+    """
     n_c, n_r = Cl.cloud_dims(10_000_000)
     c = Cl.naca0012_cloud(n_c, n_r, shuffle=True)
     W = Cl.perturbed_state(c, 0.63, 2.0)
@@ -239,13 +247,24 @@ def test_full_size_residual_parity_sampled():
         R = s.eval_residual()
         qx, qy = s.eval_q_derivatives()
     oc = oracle_for(c)
-    q = O.prim_to_q(W)
-    qx_o, qy_o = O.q_derivatives(oc, q, 2)
     rng = np.random.Generator(np.random.PCG64(4))
     idx = np.concatenate([np.arange(n_c), rng.choice(c.n, 2000, replace=False),
                           np.nonzero(c.flags == 2)[0][:200]])
-    R_o, bad = O.flux_residual_subset(oc, q, qx_o, qy_o, idx)
-    assert bad == 0
-    assert normwise(qx[idx], qx_o[idx]) < TOL_ONE_STEP
-    assert normwise(qy[idx], qy_o[idx]) < TOL_ONE_STEP
-    assert normwise(R[idx], R_o) < TOL_ONE_STEP
+
+    def oracle_eval(Win):
+        q = O.prim_to_q(Win)
+        qx_o, qy_o = O.q_derivatives(oc, q, 2)
+        R_o, bad = O.flux_residual_subset(oc, q, qx_o, qy_o, idx)
+        assert bad == 0
+        return qx_o[idx], qy_o[idx], R_o
+
+    qx_o, qy_o, R_o = oracle_eval(W)
+    eps = np.finfo(np.float64).eps
+    Wp = W * (1.0 + eps * rng.choice([-1.0, 1.0], size=W.shape))
+    qx_p, qy_p, R_p = oracle_eval(Wp)
+    for got, ref, pert in ((qx[idx], qx_o, qx_p), (qy[idx], qy_o, qy_p), (R[idx], R_o, R_p)):
+        tol = max(TOL_ONE_STEP, 8.0 * normwise(pert, ref))
+        assert tol < 1e-9  # the problem stays well within FP64
+        print(f"full-size parity: gpu-oracle {normwise(got, ref):.2e}, "
+              f"oracle 1-ulp spread {normwise(pert, ref):.2e}")
+        assert normwise(got, ref) < tol, (normwise(got, ref), normwise(pert, ref))
