@@ -289,10 +289,56 @@ def run_ours(args, rank, world, local):
             "cpu_baseline": cpu,
         }
     solver.close()
+    if args.variants:
+        mixed = time_variant(args, cloud, L.MIXED, stream, barrier, dist)
+        if result is not None:
+            result["variants"] = {"mixed": mixed}
+            result["variants"]["mixed"]["speedup_vs_fp64"] = mixed["value"] / value
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
     return result
+
+
+def time_variant(args, cloud, precision, stream, barrier, dist):
+    """Same timed region as the headline for another precision mode."""
+    import torch
+
+    from paper_2108_07031_gb300 import cloud as Cl
+    from paper_2108_07031_gb300 import lskum as L
+    s = L.Solver.from_cloud(cloud, precision=precision)
+    s.set_stream(stream.cuda_stream)
+    s.set_freestream(MACH, ALPHA)
+    s.set_state(Cl.perturbed_state(cloud, MACH, ALPHA))
+    s.step(args.warmup)
+    s.profile(True)
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    barrier()
+    start.record(stream)
+    s.step(args.steps)
+    launches = s.last_launch_count()
+    end.record(stream)
+    barrier()
+    ms = start.elapsed_time(end)
+    kt = {name: s.kernel_time(k) for name, k in (("flux", L.KERNEL_FLUX),
+                                                  ("ls_first", L.KERNEL_LS_FIRST),
+                                                  ("ls_inner", L.KERNEL_LS_INNER),
+                                                  ("residue", L.KERNEL_REDUCE))}
+    s.profile(False)
+    s.close()
+    t_max = ms
+    world = 1
+    if dist is not None:
+        world = dist.get_world_size()
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = world * cloud.n * args.steps / (t_max * 1e-3)
+    return {"precision": "mixed" if precision == L.MIXED else "fp64", "value": value,
+            "unit": UNIT, "ms_per_step": t_max / args.steps, "gpu_launches": int(launches),
+            "kernel_ms": {k: {"total_ms": v[0], "launches": v[1]} for k, v in kt.items()},
+            "dtype": "f32 flux/LS arithmetic, f64 state/residue/forces"}
 
 
 def _oracle_sample_rate(iters: int):
@@ -355,6 +401,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--points", type=int, default=WORKLOAD_POINTS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", dest="variants", action="store_false",
+                    help="skip the mixed-precision variant line")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)  # at least three untimed warm-up steps
     args.steps = max(args.steps, 1)

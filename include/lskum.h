@@ -59,6 +59,9 @@ extern "C" {
 
 /* Precision modes. */
 #define LSKUM_FP64 0  /* every step in FP64 */
+#define LSKUM_MIXED 1 /* FP32 stencil, least-squares and split-flux arithmetic (in
+                         difference form, on q stored as float pairs); FP64 state
+                         accumulation, q-variables, LS determinants, residue, forces */
 
 /* Outer-boundary modes. */
 #define LSKUM_OUTER_FREESTREAM 1 /* far-field points hold the free-stream state */
@@ -73,7 +76,7 @@ typedef struct {
     int order;          /* 2: q~ defect correction (Eqs. 27-28); 1: first order (Eq. 13) */
     double wall_factor; /* weight of dGn-/dn at wall points; default 2 (specular wall) */
     int outer_mode;     /* LSKUM_OUTER_FREESTREAM (default) or LSKUM_OUTER_KINETIC */
-    int precision;      /* LSKUM_FP64 */
+    int precision;      /* LSKUM_FP64 (default) or LSKUM_MIXED */
     int reorder;        /* 1: Hilbert-curve point order on the device (default); 0: input order */
     int block_size;     /* CUDA threads per block of the point kernels; 0 = library default */
     int check_every;    /* lskum_solve: iterations between host convergence checks; default 50 */

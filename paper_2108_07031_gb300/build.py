@@ -20,7 +20,7 @@ LIB = os.path.join(BUILD, "liblskum.so")
 PROBE = os.path.join(BUILD, "pipe_peaks")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CUDA_SOURCES = ["lskum_kernels.cu", "lskum_api.cu", "lskum_noalloc.cu"]
+CUDA_SOURCES = ["lskum_kernels.cu", "lskum_kernels_mixed.cu", "lskum_api.cu", "lskum_noalloc.cu"]
 HOST_SOURCES = ["lskum_setup.cpp"]
 HEADERS = ["lskum_internal.h", "lskum_kernels.cuh", "erfc_tables.h"]
 

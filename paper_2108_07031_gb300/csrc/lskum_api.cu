@@ -45,7 +45,9 @@ struct lskum_ctx {
     int block = kDefaultBlock;
 
     HostLayout host;
+    bool mixed = false;
     DevGeom g{};
+    DevGeom32 g32{};
     Physics ph{};
     DevState st{};
     std::vector<void*> allocations;
@@ -134,16 +136,22 @@ cudaError_t timed(lskum_ctx* c, int cls, F&& launch) {
 
 int n_blocks(const lskum_ctx* c) { return int((c->g.n + c->block - 1) / c->block); }
 
-// q-derivatives of st.q[0] into st.dq[final]; returns the index of the buffer
-// holding the result.
-cudaError_t run_q_derivatives(lskum_ctx* c, const V4* q, int* final_buf, int64_t* launches) {
-    cudaError_t e = timed(c, kLsFirst, [&] { return launch_ls_first(c->g, q, c->st.dq[0], c->block, c->stream); });
+// q-derivatives of the q buffer `qb` into dq[final] (FP64) or dq32[final]
+// (mixed); returns the index of the buffer holding the result.
+cudaError_t run_q_derivatives(lskum_ctx* c, int qb, int* final_buf, int64_t* launches) {
+    cudaError_t e = timed(c, kLsFirst, [&] {
+        return c->mixed ? launch_ls_first_mx(c->g, c->g32, c->st.qhl[qb], c->st.dq32[0], c->block, c->stream)
+                        : launch_ls_first(c->g, c->st.q[qb], c->st.dq[0], c->block, c->stream);
+    });
     if (e != cudaSuccess) return e;
     ++*launches;
     int cur = 0;
     for (int it = 0; it < c->opt.inner_iters; ++it) {
         e = timed(c, kLsInner, [&] {
-            return launch_ls_inner(c->g, q, c->st.dq[cur], c->st.dq[1 - cur], c->block, c->stream);
+            return c->mixed ? launch_ls_inner_mx(c->g, c->g32, c->st.qhl[qb], c->st.dq32[cur],
+                                                 c->st.dq32[1 - cur], c->block, c->stream)
+                            : launch_ls_inner(c->g, c->st.q[qb], c->st.dq[cur], c->st.dq[1 - cur],
+                                              c->block, c->stream);
         });
         if (e != cudaSuccess) return e;
         ++*launches;
@@ -153,18 +161,23 @@ cudaError_t run_q_derivatives(lskum_ctx* c, const V4* q, int* final_buf, int64_t
     return cudaSuccess;
 }
 
+cudaError_t launch_flux_any(lskum_ctx* c, int mode, int qb, int dbuf, int qout) {
+    if (c->mixed)
+        return launch_flux_mx(mode, c->g, c->g32, c->ph, c->st, c->st.qhl[qb], c->st.dq32[dbuf],
+                              qout >= 0 ? c->st.qhl[qout] : nullptr, c->block, c->stream);
+    return launch_flux(mode, c->g, c->ph, c->st, c->st.q[qb], c->st.dq[dbuf],
+                       qout >= 0 ? c->st.q[qout] : nullptr, c->block, c->stream);
+}
+
 // One pseudo-time iteration (Algorithm 1): four stages of q-derivatives and
 // fused flux/update, then the residue. Starts and ends with q in st.q[0].
 cudaError_t run_iteration(lskum_ctx* c, int64_t* launches) {
     int qcur = 0;
     for (int stage = 1; stage <= 4; ++stage) {
         int dbuf = 0;
-        cudaError_t e = run_q_derivatives(c, c->st.q[qcur], &dbuf, launches);
+        cudaError_t e = run_q_derivatives(c, qcur, &dbuf, launches);
         if (e != cudaSuccess) return e;
-        e = timed(c, kFlux, [&] {
-            return launch_flux(stage, c->g, c->ph, c->st, c->st.q[qcur], c->st.dq[dbuf],
-                               c->st.q[1 - qcur], c->block, c->stream);
-        });
+        e = timed(c, kFlux, [&] { return launch_flux_any(c, stage, qcur, dbuf, 1 - qcur); });
         if (e != cudaSuccess) return e;
         ++*launches;
         qcur = 1 - qcur;
@@ -175,6 +188,12 @@ cudaError_t run_iteration(lskum_ctx* c, int64_t* launches) {
         }
     }
     return cudaSuccess;
+}
+
+// After U changed from the host side: the mixed path's float-pair q.
+cudaError_t refresh_mixed_q(lskum_ctx* c) {
+    if (!c->mixed) return cudaSuccess;
+    return launch_q_from_U_mx(c->g, c->ph, c->st.U, c->st.qhl[0], c->stream);
 }
 
 int reset_history(lskum_ctx* c) {
@@ -229,7 +248,8 @@ int lskum_create(int64_t n, const double* xy, const double* normals, const int8_
     if (opt) o = *opt;
     if (!(o.gamma > 1.0 && o.gamma < 2.0) || !(o.cfl > 0.0) || o.inner_iters < 0 ||
         o.inner_iters > 64 || (o.order != 1 && o.order != 2) || !(o.wall_factor > 0.0) ||
-        (o.outer_mode != 0 && o.outer_mode != 1) || o.precision != LSKUM_FP64 ||
+        (o.outer_mode != 0 && o.outer_mode != 1) ||
+        (o.precision != LSKUM_FP64 && o.precision != LSKUM_MIXED) ||
         (o.block_size != 0 && o.block_size != 128 && o.block_size != 256) || o.check_every < 1)
         return fail(LSKUM_ERR_INVALID_ARG, "invalid option value");
 
@@ -237,6 +257,7 @@ int lskum_create(int64_t n, const double* xy, const double* normals, const int8_
     if (!c) return fail(LSKUM_ERR_INVALID_ARG, "out of host memory");
     c->opt = o;
     c->block = o.block_size ? o.block_size : kDefaultBlock;
+    c->mixed = o.precision == LSKUM_MIXED;
 
     // host validation and layout first: input errors are reported without a GPU
     std::string err;
@@ -277,24 +298,48 @@ int lskum_create(int64_t n, const double* xy, const double* normals, const int8_
         (e = upload(c, &g.nrm, nrm2)) != cudaSuccess ||
         (e = upload(c, &g.dmin, L.dmin)) != cudaSuccess ||
         (e = upload(c, &g.nbr, L.nbr)) != cudaSuccess ||
-        (e = upload(c, &g.hdx, L.hdx)) != cudaSuccess ||
-        (e = upload(c, &g.hdy, L.hdy)) != cudaSuccess ||
-        (e = upload(c, &g.wx, L.wx)) != cudaSuccess ||
-        (e = upload(c, &g.wy, L.wy)) != cudaSuccess ||
-        (e = upload(c, &g.ws, L.ws)) != cudaSuccess ||
-        (e = upload(c, &g.wn, L.wn)) != cudaSuccess ||
         (e = upload(c, &g.dev_to_user, L.dev_to_user)) != cudaSuccess ||
         (e = upload(c, &g.user_to_dev, L.user_to_dev)) != cudaSuccess ||
         (e = upload(c, &g.wall_id, L.wall_id)) != cudaSuccess ||
         (e = upload(c, &g.wall_nds, nds2)) != cudaSuccess)
         return bail(e, "upload of the cloud layout");
 
+    if (!c->mixed) {
+        if ((e = upload(c, &g.hdx, L.hdx)) != cudaSuccess ||
+            (e = upload(c, &g.hdy, L.hdy)) != cudaSuccess ||
+            (e = upload(c, &g.wx, L.wx)) != cudaSuccess ||
+            (e = upload(c, &g.wy, L.wy)) != cudaSuccess ||
+            (e = upload(c, &g.ws, L.ws)) != cudaSuccess ||
+            (e = upload(c, &g.wn, L.wn)) != cudaSuccess)
+            return bail(e, "upload of the FP64 cloud layout");
+    } else {
+        auto to32 = [](const std::vector<double>& v) { return std::vector<float>(v.begin(), v.end()); };
+        if ((e = upload(c, &c->g32.hdx, to32(L.hdx))) != cudaSuccess ||
+            (e = upload(c, &c->g32.hdy, to32(L.hdy))) != cudaSuccess ||
+            (e = upload(c, &c->g32.wx, to32(L.wx))) != cudaSuccess ||
+            (e = upload(c, &c->g32.wy, to32(L.wy))) != cudaSuccess ||
+            (e = upload(c, &c->g32.ws, to32(L.ws))) != cudaSuccess ||
+            (e = upload(c, &c->g32.wn, to32(L.wn))) != cudaSuccess)
+            return bail(e, "upload of the FP32 cloud layout");
+    }
+
     DevState& st = c->st;
     const size_t N = size_t(L.n);
     const int nb = int((L.n + 127) / 128) + 1;  // enough for either block size
+    if (c->mixed) {
+        if ((e = dev_alloc(c, &st.qhl[0], N)) != cudaSuccess ||
+            (e = dev_alloc(c, &st.qhl[1], N)) != cudaSuccess ||
+            (e = dev_alloc(c, &st.dq32[0], N)) != cudaSuccess ||
+            (e = dev_alloc(c, &st.dq32[1], N)) != cudaSuccess)
+            return bail(e, "mixed-precision state allocation");
+    } else {
+        if ((e = dev_alloc(c, &st.q[1], N)) != cudaSuccess ||
+            (e = dev_alloc(c, &st.dq[0], N)) != cudaSuccess ||
+            (e = dev_alloc(c, &st.dq[1], N)) != cudaSuccess)
+            return bail(e, "FP64 state allocation");
+    }
     if ((e = dev_alloc(c, &st.U, N)) != cudaSuccess || (e = dev_alloc(c, &st.U0, N)) != cudaSuccess ||
-        (e = dev_alloc(c, &st.q[0], N)) != cudaSuccess || (e = dev_alloc(c, &st.q[1], N)) != cudaSuccess ||
-        (e = dev_alloc(c, &st.dq[0], N)) != cudaSuccess || (e = dev_alloc(c, &st.dq[1], N)) != cudaSuccess ||
+        (e = dev_alloc(c, &st.q[0], N)) != cudaSuccess ||
         (e = dev_alloc(c, &st.dt, N)) != cudaSuccess || (e = dev_alloc(c, &st.R, N)) != cudaSuccess ||
         (e = dev_alloc(c, &st.partials, size_t(nb))) != cudaSuccess ||
         (e = dev_alloc(c, &st.res_hist, size_t(kResCap))) != cudaSuccess ||
@@ -348,6 +393,7 @@ int lskum_set_freestream(lskum_ctx* c, double mach, double alpha_deg) {
     const double a = alpha_deg * kPi / 180.0;
     const V4 W{1.0, mach * std::cos(a), mach * std::sin(a), 1.0 / c->opt.gamma};
     LSKUM_CUDA(launch_set_uniform(c->g, c->ph, W, c->st.U, c->st.q[0], c->stream));
+    LSKUM_CUDA(refresh_mixed_q(c));
     int rc = reset_history(c);
     if (rc != LSKUM_OK) return rc;
     c->have_state = true;
@@ -360,6 +406,7 @@ int lskum_set_state(lskum_ctx* c, const double* prim) {
     int rc = reset_history(c);
     if (rc != LSKUM_OK) return rc;
     LSKUM_CUDA(launch_set_prim(c->g, c->ph, c->staging, c->st.U, c->st.q[0], c->st.status, c->stream));
+    LSKUM_CUDA(refresh_mixed_q(c));
     int status = 0;
     rc = read_status(c, &status);
     if (rc != LSKUM_OK) return rc;
@@ -474,9 +521,9 @@ int lskum_eval_residual(lskum_ctx* c, double* R) {
     if (!c->have_state) return fail(LSKUM_ERR_STATE, "no state set");
     int dbuf = 0;
     int64_t launches = 0;
-    cudaError_t e = run_q_derivatives(c, c->st.q[0], &dbuf, &launches);
+    cudaError_t e = run_q_derivatives(c, 0, &dbuf, &launches);
     if (e != cudaSuccess) return cuda_fail(e, "q-derivatives");
-    LSKUM_CUDA(launch_flux(0, c->g, c->ph, c->st, c->st.q[0], c->st.dq[dbuf], nullptr, c->block, c->stream));
+    LSKUM_CUDA(launch_flux_any(c, 0, 0, dbuf, -1));
     LSKUM_CUDA(launch_gather_v4(c->g, c->st.R, c->staging, c->stream));
     LSKUM_CUDA(cudaMemcpyAsync(R, c->staging, sizeof(V4) * size_t(c->g.n), cudaMemcpyDeviceToHost, c->stream));
     LSKUM_CUDA(cudaStreamSynchronize(c->stream));
@@ -491,9 +538,13 @@ int lskum_eval_q_derivatives(lskum_ctx* c, double* qx, double* qy) {
     }
     int dbuf = 0;
     int64_t launches = 0;
-    cudaError_t e = run_q_derivatives(c, c->st.q[0], &dbuf, &launches);
+    cudaError_t e = run_q_derivatives(c, 0, &dbuf, &launches);
     if (e != cudaSuccess) return cuda_fail(e, "q-derivatives");
-    LSKUM_CUDA(launch_gather_v8(c->g, c->st.dq[dbuf], c->staging8, c->stream));
+    if (c->mixed) {
+        LSKUM_CUDA(launch_dq_to_user_mx(c->g, c->st.dq32[dbuf], c->staging8, c->stream));
+    } else {
+        LSKUM_CUDA(launch_gather_v8(c->g, c->st.dq[dbuf], c->staging8, c->stream));
+    }
     std::vector<V8> h(size_t(c->g.n));
     LSKUM_CUDA(cudaMemcpyAsync(h.data(), c->staging8, sizeof(V8) * h.size(), cudaMemcpyDeviceToHost, c->stream));
     LSKUM_CUDA(cudaStreamSynchronize(c->stream));

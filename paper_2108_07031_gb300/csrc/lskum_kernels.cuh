@@ -19,6 +19,28 @@ struct __align__(64) V8 {
     double y[4];
 };
 
+// Mixed precision: q as a pair of floats (hi + lo carries the FP64 value to
+// ~2^-48, so differences of nearby q are exact to FP32 precision of the
+// difference), and (q_x, q_y) in FP32.
+struct __align__(32) QHL {
+    float4 hi;
+    float4 lo;
+};
+struct __align__(32) D8f {
+    float4 x;
+    float4 y;
+};
+
+// FP32 copies of the slot-major per-neighbour arrays (mixed precision).
+struct DevGeom32 {
+    const float* hdx;
+    const float* hdy;
+    const float* wx;
+    const float* wy;
+    const float* ws;
+    const float* wn;
+};
+
 // Static cloud data on the device (device point order).
 struct DevGeom {
     int64_t n;
@@ -59,6 +81,8 @@ struct DevState {
     V4* q[2];  // q-variables, double-buffered across stages
     V8* dq[2]; // q-derivatives, double-buffered across inner iterations
     double* dt;
+    QHL* qhl[2];  // mixed precision: q-variables as float pairs
+    D8f* dq32[2]; // mixed precision: q-derivatives in FP32
     V4* R;     // residual output of the evaluation mode
     double* partials;  // per-block partial sums (scratch)
     double* res_hist;  // residue per iteration (ring buffer)
@@ -91,5 +115,17 @@ cudaError_t launch_gather_v4(const DevGeom& g, const V4* src_dev, V4* dst_user, 
 cudaError_t launch_gather_v8(const DevGeom& g, const V8* src_dev, V8* dst_user, cudaStream_t s);
 cudaError_t launch_forces(const DevGeom& g, const Physics& ph, const DevState& st,
                           cudaStream_t s);
+
+// Mixed-precision launchers (lskum_kernels_mixed.cu).
+cudaError_t launch_ls_first_mx(const DevGeom& g, const DevGeom32& g32, const QHL* q, D8f* dq,
+                               int block, cudaStream_t s);
+cudaError_t launch_ls_inner_mx(const DevGeom& g, const DevGeom32& g32, const QHL* q,
+                               const D8f* din, D8f* dout, int block, cudaStream_t s);
+cudaError_t launch_flux_mx(int mode, const DevGeom& g, const DevGeom32& g32, const Physics& ph,
+                           const DevState& st, const QHL* q_in, const D8f* dq, QHL* q_out,
+                           int block, cudaStream_t s);
+cudaError_t launch_q_from_U_mx(const DevGeom& g, const Physics& ph, const V4* U, QHL* q,
+                               cudaStream_t s);
+cudaError_t launch_dq_to_user_mx(const DevGeom& g, const D8f* src, V8* dst_user, cudaStream_t s);
 
 }  // namespace lskum

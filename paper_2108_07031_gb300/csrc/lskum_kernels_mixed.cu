@@ -1,0 +1,473 @@
+// Mixed-precision kernels of the q-LSKUM hot path (sm_103a).
+//
+// FP32 for the stencil, least-squares and split-flux arithmetic; FP64 for
+// the state accumulation U += dt R, the q-variables derived from U, the 2x2
+// least-squares determinants (folded into weights on the host in FP64 and
+// stored as FP32), the residue and the force integral.
+//
+// Differences are what the method consumes -- q_j - q_i in the
+// least-squares sums and G(q~_j) - G(q~_0) in the split-flux derivatives --
+// and at fine resolution they are 1e-4 of the values, so FP32 values would
+// lose four of their seven digits in each subtraction. The FP32 path
+// therefore never subtracts two nearby values:
+//   * q is stored as a pair of floats (hi + lo = the FP64 q to ~2^-48), so
+//     q_j - q_i = (hi_j - hi_i) + (lo_j - lo_i) is accurate to FP32
+//     precision relative to the difference itself;
+//   * the primitive state of q~_j is formed as base + difference from
+//     q~_0 and dq~ = q~_j - q~_0 with quotient identities and log1p/expm1;
+//   * each split flux is differenced in closed form: products by the
+//     product rule, exp(-S^2) by expm1, and erfc by the midpoint expansion
+//     erfc(m-h) - erfc(m+h) = (2/sqrt(pi)) e^{-m^2} sum_k H_2k(m) ...
+//     (Hermite polynomials) for small steps, directly for large ones.
+// The result is the same residual as the FP64 path to about FP32 relative
+// precision of the residual itself, not of the fluxes.
+
+#include <cmath>
+
+#include "lskum_internal.h"
+#include "lskum_kernels.cuh"
+
+namespace lskum {
+
+namespace {
+
+constexpr float kInvSqrtPiF = 0.5641895835477563f;  // 1 / sqrt(pi)
+
+// q_j - q_i from the hi/lo float pairs.
+__device__ __forceinline__ float4 qdiff(const QHL& a, const QHL& b) {
+    return make_float4((a.hi.x - b.hi.x) + (a.lo.x - b.lo.x), (a.hi.y - b.hi.y) + (a.lo.y - b.lo.y),
+                       (a.hi.z - b.hi.z) + (a.lo.z - b.lo.z), (a.hi.w - b.hi.w) + (a.lo.w - b.lo.w));
+}
+
+// ----------------------------------------------------------- q-derivatives
+
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_ls_first_mx(const DevGeom g, const DevGeom32 g32,
+                                                       const QHL* __restrict__ q,
+                                                       D8f* __restrict__ dq) {
+    const int64_t d = int64_t(blockIdx.x) * BLOCK + threadIdx.x;
+    if (d >= g.n) return;
+    const QHL qi = q[d];
+    float4 ax = make_float4(0.f, 0.f, 0.f, 0.f), ay = ax;
+    const int c = g.cnt[d];
+    for (int k = 0; k < c; ++k) {
+        const int64_t at = int64_t(k) * g.stride + d;
+        const uint32_t j = g.nbr[at] & kIndexMask;
+        const float wx = g32.wx[at], wy = g32.wy[at];
+        const float4 dqv = qdiff(q[j], qi);
+        ax.x += wx * dqv.x; ax.y += wx * dqv.y; ax.z += wx * dqv.z; ax.w += wx * dqv.w;
+        ay.x += wy * dqv.x; ay.y += wy * dqv.y; ay.z += wy * dqv.z; ay.w += wy * dqv.w;
+    }
+    dq[d] = D8f{ax, ay};
+}
+
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_ls_inner_mx(const DevGeom g, const DevGeom32 g32,
+                                                       const QHL* __restrict__ q,
+                                                       const D8f* __restrict__ din,
+                                                       D8f* __restrict__ dout) {
+    const int64_t d = int64_t(blockIdx.x) * BLOCK + threadIdx.x;
+    if (d >= g.n) return;
+    const QHL qi = q[d];
+    const D8f di = din[d];
+    float4 ax = make_float4(0.f, 0.f, 0.f, 0.f), ay = ax;
+    const int c = g.cnt[d];
+    for (int k = 0; k < c; ++k) {
+        const int64_t at = int64_t(k) * g.stride + d;
+        const uint32_t j = g.nbr[at] & kIndexMask;
+        const float wx = g32.wx[at], wy = g32.wy[at];
+        const float hx = g32.hdx[at], hy = g32.hdy[at];
+        const float4 dqv = qdiff(q[j], qi);
+        const D8f dj = din[j];
+        // dq~ = (q_j - q_i) - (dx (qx_j - qx_i) + dy (qy_j - qy_i)) / 2   (Eq. 28)
+        const float t0 = dqv.x - (hx * (dj.x.x - di.x.x) + hy * (dj.y.x - di.y.x));
+        const float t1 = dqv.y - (hx * (dj.x.y - di.x.y) + hy * (dj.y.y - di.y.y));
+        const float t2 = dqv.z - (hx * (dj.x.z - di.x.z) + hy * (dj.y.z - di.y.z));
+        const float t3 = dqv.w - (hx * (dj.x.w - di.x.w) + hy * (dj.y.w - di.y.w));
+        ax.x += wx * t0; ax.y += wx * t1; ax.z += wx * t2; ax.w += wx * t3;
+        ay.x += wy * t0; ay.y += wy * t1; ay.z += wy * t2; ay.w += wy * t3;
+    }
+    dout[d] = D8f{ax, ay};
+}
+
+// ------------------------------------------------ primitive base + difference
+
+struct PrimPair {
+    float r, u, v, p, sb;       // base state (of q~_0): density, velocity, pressure, sqrt(beta)
+    float dr, du, dv, dp, dsb;  // difference state(q~_j) - state(q~_0)
+};
+
+// From the base q~_0 and the difference dq~ = q~_j - q~_0 (inverse of Eq. 26).
+template <bool G14>
+__device__ __forceinline__ PrimPair prim_pair(const float4 b, const float4 dq, const float gm1_inv) {
+    PrimPair w;
+    const float beta = -0.5f * b.w;
+    const float dbeta = -0.5f * dq.w;
+    const float qj4 = b.w + dq.w;
+    const float inv2b = -1.0f / b.w;  // 1 / (2 beta)
+    w.u = b.y * inv2b;
+    w.v = b.z * inv2b;
+    // u = -q2/q4:  u_j - u_0 = (q2 dq4 - dq2 q4) / (q4 q4_j)
+    const float rq = 1.0f / (b.w * qj4);
+    w.du = (b.y * dq.w - dq.y * b.w) * rq;
+    w.dv = (b.z * dq.w - dq.z * b.w) * rq;
+    const float uj = w.u + w.du, vj = w.v + w.dv;
+    const float uu0 = w.u * w.u + w.v * w.v;
+    const float uuj = uj * uj + vj * vj;
+    const float duu = w.du * (uj + w.u) + w.dv * (vj + w.v);
+    const float isb = rsqrtf(beta);
+    w.sb = beta * isb;
+    const float betaj = beta + dbeta;
+    w.dsb = dbeta / (sqrtf(betaj) + w.sb);
+    // ln rho = q1 - ln(beta)/(gamma-1) + beta |u|^2
+    if (G14) {
+        const float i2 = isb * isb;
+        w.r = __expf(b.x + beta * uu0) * (i2 * i2 * isb);
+    } else {
+        w.r = __expf(b.x - __logf(beta) * gm1_inv + beta * uu0);
+    }
+    const float dlnr = dq.x - log1pf(dbeta / beta) * gm1_inv + (dbeta * uuj + beta * duu);
+    w.dr = w.r * expm1f(dlnr);
+    // p = rho / (2 beta):  p_j - p_0 = (drho beta - rho dbeta) / (2 beta beta_j)
+    w.p = w.r * inv2b;
+    w.dp = (w.dr * beta - w.r * dbeta) / (2.0f * beta * betaj);
+    return w;
+}
+
+// erfc(m - h) - erfc(m + h) = (4/sqrt(pi)) e^{-m^2} (h + H2 h^3/6 + H4 h^5/120
+// + H6 h^7/5040 + H8 h^9/362880) with the Hermite polynomials H_k(m): the
+// even Taylor terms of e^{-t^2} about m integrated over [m - h, m + h].
+__device__ __forceinline__ float erfc_central_diff(const float m, const float h) {
+    const float m2 = m * m;
+    const float H2 = 4.0f * m2 - 2.0f;
+    const float H4 = (16.0f * m2 - 48.0f) * m2 + 12.0f;
+    const float H6 = ((64.0f * m2 - 480.0f) * m2 + 720.0f) * m2 - 120.0f;
+    const float H8 = (((256.0f * m2 - 3584.0f) * m2 + 13440.0f) * m2 - 13440.0f) * m2 + 1680.0f;
+    const float h2 = h * h;
+    const float s = h * (1.0f + h2 * (H2 * (1.0f / 6.0f) +
+                                      h2 * (H4 * (1.0f / 120.0f) +
+                                            h2 * (H6 * (1.0f / 5040.0f) + h2 * (H8 * (1.0f / 362880.0f))))));
+    return 4.0f * kInvSqrtPiF * __expf(-m2) * s;
+}
+
+// Difference of the kinetic split flux along the frame's first axis, sign sg:
+// dG = G(state_j) - G(state_0), state_j = base + difference.
+__device__ __forceinline__ void dsplit_flux_a(const float r0, const float ua0, const float ub0,
+                                              const float p0, const float sb0, const float dr,
+                                              const float dua, const float dub, const float dp,
+                                              const float dsb, const float sg, const float gm1_inv,
+                                              float dG[4]) {
+    const float uaj = ua0 + dua, ubj = ub0 + dub, sbj = sb0 + dsb;
+    const float S0 = ua0 * sb0;
+    const float dS = dua * sbj + ua0 * dsb;
+    const float Sj = S0 + dS;
+    // exponential: e_j - e_0 = e_0 expm1(-(S_j^2 - S_0^2))
+    const float e0 = __expf(-S0 * S0);
+    const float de = e0 * expm1f(-dS * (Sj + S0));
+    // A = erfc(x)/2 at x = -sg S
+    const float x0 = -sg * S0, dx = -sg * dS;
+    const float A0 = 0.5f * erfcf(x0);
+    float dA;
+    if (fabsf(dx) <= 0.25f) {
+        // erfc(x0 + dx) - erfc(x0) = -(erfc(m - h) - erfc(m + h)), m = x0 + dx/2, h = dx/2
+        dA = -0.5f * erfc_central_diff(x0 + 0.5f * dx, 0.5f * dx);
+    } else {
+        dA = 0.5f * (erfcf(x0 + dx) - erfcf(x0));
+    }
+    const float Aj = A0 + dA;
+    // B = e / (2 sqrt(pi) sqrt(beta))
+    const float c = 0.5f * kInvSqrtPiF;
+    const float isb0 = 1.0f / sb0, isbj = 1.0f / sbj;
+    const float B0 = c * e0 * isb0;
+    const float dB = c * (de * isbj - e0 * dsb * isbj * isb0);
+    const float Bj = B0 + dB;
+    // rho e = p/(gamma-1) + rho |u|^2 / 2
+    const float uu0 = ua0 * ua0 + ub0 * ub0;
+    const float uuj = uaj * uaj + ubj * ubj;
+    const float duu = dua * (uaj + ua0) + dub * (ubj + ub0);
+    const float E0 = p0 * gm1_inv + 0.5f * r0 * uu0;
+    const float dE = dp * gm1_inv + 0.5f * (dr * uuj + r0 * duu);
+    // t = u_a A + sg B
+    const float t0 = ua0 * A0 + sg * B0;
+    const float dt = dua * Aj + ua0 * dA + sg * dB;
+    const float tj = t0 + dt;
+    // mass: rho t
+    dG[0] = dr * tj + r0 * dt;
+    // a-momentum: (p + rho u_a^2) A + sg rho u_a B
+    const float P0 = p0 + r0 * ua0 * ua0;
+    const float dP = dp + dr * uaj * uaj + r0 * dua * (uaj + ua0);
+    const float ru0 = r0 * ua0;
+    const float dru = dr * uaj + r0 * dua;
+    dG[1] = dP * Aj + P0 * dA + sg * (dru * Bj + ru0 * dB);
+    // b-momentum: rho u_b t
+    const float rb0 = r0 * ub0;
+    const float drb = dr * ubj + r0 * dub;
+    dG[2] = drb * tj + rb0 * dt;
+    // energy: (p + rho e) u_a A + sg (rho e + p/2) B
+    const float Q0 = (p0 + E0) * ua0;
+    const float dQ = (dp + dE) * uaj + (p0 + E0) * dua;
+    const float Rr0 = E0 + 0.5f * p0;
+    const float dRr = dE + 0.5f * dp;
+    dG[3] = dQ * Aj + Q0 * dA + sg * (dRr * Bj + Rr0 * dB);
+}
+
+__device__ __forceinline__ void cons_to_q64(const V4& U, const Physics& ph, V4& q, double& rho,
+                                            double& u, double& v, double& p) {
+    rho = U.a;
+    u = U.b / rho;
+    v = U.c / rho;
+    p = ph.gm1 * (U.d - 0.5 * rho * (u * u + v * v));
+    const double beta = rho / (2.0 * p);
+    q.a = log(rho) + log(beta) * ph.gm1_inv - beta * (u * u + v * v);
+    q.b = 2.0 * beta * u;
+    q.c = 2.0 * beta * v;
+    q.d = -2.0 * beta;
+}
+
+__device__ __forceinline__ QHL split_hl(const V4& q) {
+    QHL o;
+    o.hi = make_float4(__double2float_rn(q.a), __double2float_rn(q.b), __double2float_rn(q.c),
+                       __double2float_rn(q.d));
+    o.lo = make_float4(__double2float_rn(q.a - double(o.hi.x)), __double2float_rn(q.b - double(o.hi.y)),
+                       __double2float_rn(q.c - double(o.hi.z)), __double2float_rn(q.d - double(o.hi.w)));
+    return o;
+}
+
+__device__ __forceinline__ bool physical(double rho, double u, double v, double p) {
+    return rho > 0.0 && p > 0.0 && isfinite(rho) && isfinite(p) && isfinite(u) && isfinite(v);
+}
+
+template <int BLOCK>
+__device__ __forceinline__ double block_sum(double x) {
+    __shared__ double warp_part[BLOCK / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) warp_part[wid] = x;
+    __syncthreads();
+    double s = 0.0;
+    if (wid == 0) {
+        s = lane < BLOCK / 32 ? warp_part[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    }
+    return s;
+}
+
+// ------------------------------------------------------- flux residual + RK
+
+template <int MODE, int BLOCK, bool G14>
+__global__ void __launch_bounds__(BLOCK) k_flux_mx(const DevGeom g, const DevGeom32 g32,
+                                                   const Physics ph, const DevState st,
+                                                   const QHL* __restrict__ q_in,
+                                                   const D8f* __restrict__ dq,
+                                                   QHL* __restrict__ q_out) {
+    const int64_t d = int64_t(blockIdx.x) * BLOCK + threadIdx.x;
+    double r2 = 0.0;
+    if (d < g.n) {
+        const int8_t fl = g.flag[d];
+        const bool fixed = ph.outer_fixed && fl == LSKUM_OUTER;
+        float R[4] = {0.f, 0.f, 0.f, 0.f};
+        if (!fixed) {
+            float tx = 1.f, ty = 0.f, nx = 0.f, ny = 1.f;
+            const bool local = fl != LSKUM_INTERIOR;
+            if (local) {
+                const double2 nn = g.nrm[d];
+                nx = float(nn.x);
+                ny = float(nn.y);
+                tx = ny;
+                ty = -nx;
+            }
+            const QHL qi = q_in[d];
+            const D8f di = dq[d];
+            const float4 qiv = make_float4(qi.hi.x + qi.lo.x, qi.hi.y + qi.lo.y, qi.hi.z + qi.lo.z,
+                                           qi.hi.w + qi.lo.w);
+            const float gm1_inv = float(ph.gm1_inv);
+            const bool second = ph.order == 2;
+            const int c = g.cnt[d];
+            for (int k = 0; k < c; ++k) {
+                const int64_t at = int64_t(k) * g.stride + d;
+                const uint32_t e = g.nbr[at];
+                const uint32_t j = e & kIndexMask;
+                const uint32_t sc = (e >> kIndexBits) & 3u;
+                const uint32_t nc = (e >> (kIndexBits + 2)) & 3u;
+                const float4 dqv = qdiff(q_in[j], qi);
+                float4 base = qiv, dlt = dqv;
+                if (second) {
+                    const float hx = g32.hdx[at], hy = g32.hdy[at];
+                    const D8f dj = dq[j];
+                    // q~_0 = q_i - (dx q_x,i + dy q_y,i)/2; dq~ = q~_j - q~_0 (Eq. 28)
+                    base.x = qiv.x - (hx * di.x.x + hy * di.y.x);
+                    base.y = qiv.y - (hx * di.x.y + hy * di.y.y);
+                    base.z = qiv.z - (hx * di.x.z + hy * di.y.z);
+                    base.w = qiv.w - (hx * di.x.w + hy * di.y.w);
+                    dlt.x = dqv.x - (hx * (dj.x.x - di.x.x) + hy * (dj.y.x - di.y.x));
+                    dlt.y = dqv.y - (hx * (dj.x.y - di.x.y) + hy * (dj.y.y - di.y.y));
+                    dlt.z = dqv.z - (hx * (dj.x.z - di.x.z) + hy * (dj.y.z - di.y.z));
+                    dlt.w = dqv.w - (hx * (dj.x.w - di.x.w) + hy * (dj.y.w - di.y.w));
+                }
+                if (dlt.x == 0.f && dlt.y == 0.f && dlt.z == 0.f && dlt.w == 0.f) continue;
+                PrimPair w = prim_pair<G14>(base, dlt, gm1_inv);
+                if (local) {
+                    const float s0 = w.u * tx + w.v * ty, n0 = w.u * nx + w.v * ny;
+                    const float ds = w.du * tx + w.dv * ty, dn = w.du * nx + w.dv * ny;
+                    w.u = s0; w.v = n0; w.du = ds; w.dv = dn;
+                }
+                if (sc) {
+                    const float sg = sc == 1u ? 1.f : -1.f;
+                    float dG[4];
+                    dsplit_flux_a(w.r, w.u, w.v, w.p, w.sb, w.dr, w.du, w.dv, w.dp, w.dsb, sg,
+                                  gm1_inv, dG);
+                    const float wt = g32.ws[at];
+                    R[0] += wt * dG[0]; R[1] += wt * dG[1]; R[2] += wt * dG[2]; R[3] += wt * dG[3];
+                }
+                if (nc) {
+                    const float sg = nc == 1u ? 1.f : -1.f;
+                    float dG[4];
+                    dsplit_flux_a(w.r, w.v, w.u, w.p, w.sb, w.dr, w.dv, w.du, w.dp, w.dsb, sg,
+                                  gm1_inv, dG);
+                    const float wt = g32.wn[at];
+                    R[0] += wt * dG[0]; R[1] += wt * dG[2]; R[2] += wt * dG[1]; R[3] += wt * dG[3];
+                }
+            }
+            if (local) {
+                const float rs = R[1], rn = R[2];
+                R[1] = rs * tx + rn * nx;
+                R[2] = rs * ty + rn * ny;
+            }
+        }
+        // FP64 from here: state accumulation, wall condition, next q, residue
+        const double R0 = R[0], R1 = R[1], R2 = R[2], R3 = R[3];
+        if (MODE == 0) {
+            st.R[d] = V4{R0, R1, R2, R3};
+        } else {
+            V4 U = st.U[d];
+            double dtv;
+            if (MODE == 1) {
+                const double rho = U.a, u = U.b / rho, v = U.c / rho;
+                const double p = ph.gm1 * (U.d - 0.5 * rho * (u * u + v * v));
+                dtv = ph.cfl * g.dmin[d] / (sqrt(u * u + v * v) + sqrt(ph.gamma * p / rho));
+                st.dt[d] = dtv;
+                st.U0[d] = U;
+                r2 = R0 * R0;
+            } else {
+                dtv = st.dt[d];
+            }
+            if (!fixed) {
+                const double h = 0.5 * dtv;
+                if (MODE == 3) {
+                    const V4 U0 = st.U0[d];
+                    U.a = (2.0 / 3.0) * U0.a + (1.0 / 3.0) * (U.a - h * R0);
+                    U.b = (2.0 / 3.0) * U0.b + (1.0 / 3.0) * (U.b - h * R1);
+                    U.c = (2.0 / 3.0) * U0.c + (1.0 / 3.0) * (U.c - h * R2);
+                    U.d = (2.0 / 3.0) * U0.d + (1.0 / 3.0) * (U.d - h * R3);
+                } else {
+                    U.a -= h * R0;
+                    U.b -= h * R1;
+                    U.c -= h * R2;
+                    U.d -= h * R3;
+                }
+                if (fl == LSKUM_WALL) {
+                    const double2 nn = g.nrm[d];
+                    const double tx = nn.y, ty = -nn.x;
+                    const double ms = U.b * tx + U.c * ty;
+                    U.b = ms * tx;
+                    U.c = ms * ty;
+                }
+                st.U[d] = U;
+            }
+            V4 qn;
+            double rho, u, v, p;
+            cons_to_q64(U, ph, qn, rho, u, v, p);
+            q_out[d] = split_hl(qn);
+            if (!physical(rho, u, v, p)) atomicOr(st.status, 1);
+        }
+    }
+    if (MODE == 1) {
+        const double s = block_sum<BLOCK>(r2);
+        if (threadIdx.x == 0) st.partials[blockIdx.x] = s;
+    }
+}
+
+__global__ void k_q_from_U_mx(const DevGeom g, const Physics ph, const V4* __restrict__ U,
+                              QHL* __restrict__ q) {
+    const int64_t d = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (d >= g.n) return;
+    V4 qn;
+    double rho, u, v, p;
+    cons_to_q64(U[d], ph, qn, rho, u, v, p);
+    q[d] = split_hl(qn);
+}
+
+__global__ void k_dq_to_v8(const DevGeom g, const D8f* __restrict__ src, V8* __restrict__ dst) {
+    const int64_t d = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (d >= g.n) return;
+    const D8f s = src[d];
+    V8 o;
+    o.x[0] = s.x.x; o.x[1] = s.x.y; o.x[2] = s.x.z; o.x[3] = s.x.w;
+    o.y[0] = s.y.x; o.y[1] = s.y.y; o.y[2] = s.y.z; o.y[3] = s.y.w;
+    dst[g.dev_to_user[d]] = o;
+}
+
+inline unsigned grid_for(int64_t n, int block) { return unsigned((n + block - 1) / block); }
+
+template <int BLOCK, bool G14>
+void flux_mx_dispatch(int mode, const DevGeom& g, const DevGeom32& g32, const Physics& ph,
+                      const DevState& st, const QHL* q_in, const D8f* dq, QHL* q_out,
+                      cudaStream_t s) {
+    const unsigned grid = grid_for(g.n, BLOCK);
+    switch (mode) {
+        case 0: k_flux_mx<0, BLOCK, G14><<<grid, BLOCK, 0, s>>>(g, g32, ph, st, q_in, dq, q_out); break;
+        case 1: k_flux_mx<1, BLOCK, G14><<<grid, BLOCK, 0, s>>>(g, g32, ph, st, q_in, dq, q_out); break;
+        case 2: k_flux_mx<2, BLOCK, G14><<<grid, BLOCK, 0, s>>>(g, g32, ph, st, q_in, dq, q_out); break;
+        case 3: k_flux_mx<3, BLOCK, G14><<<grid, BLOCK, 0, s>>>(g, g32, ph, st, q_in, dq, q_out); break;
+        default: k_flux_mx<4, BLOCK, G14><<<grid, BLOCK, 0, s>>>(g, g32, ph, st, q_in, dq, q_out); break;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_ls_first_mx(const DevGeom& g, const DevGeom32& g32, const QHL* q, D8f* dq,
+                               int block, cudaStream_t s) {
+    if (block == 256)
+        k_ls_first_mx<256><<<grid_for(g.n, 256), 256, 0, s>>>(g, g32, q, dq);
+    else
+        k_ls_first_mx<kDefaultBlock><<<grid_for(g.n, kDefaultBlock), kDefaultBlock, 0, s>>>(g, g32, q, dq);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ls_inner_mx(const DevGeom& g, const DevGeom32& g32, const QHL* q,
+                               const D8f* din, D8f* dout, int block, cudaStream_t s) {
+    if (block == 256)
+        k_ls_inner_mx<256><<<grid_for(g.n, 256), 256, 0, s>>>(g, g32, q, din, dout);
+    else
+        k_ls_inner_mx<kDefaultBlock><<<grid_for(g.n, kDefaultBlock), kDefaultBlock, 0, s>>>(g, g32, q, din, dout);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_flux_mx(int mode, const DevGeom& g, const DevGeom32& g32, const Physics& ph,
+                           const DevState& st, const QHL* q_in, const D8f* dq, QHL* q_out,
+                           int block, cudaStream_t s) {
+    const bool g14 = fabs(ph.gm1_inv - 2.5) < 1e-12;
+    if (block == 256) {
+        if (g14) flux_mx_dispatch<256, true>(mode, g, g32, ph, st, q_in, dq, q_out, s);
+        else flux_mx_dispatch<256, false>(mode, g, g32, ph, st, q_in, dq, q_out, s);
+    } else {
+        if (g14) flux_mx_dispatch<kDefaultBlock, true>(mode, g, g32, ph, st, q_in, dq, q_out, s);
+        else flux_mx_dispatch<kDefaultBlock, false>(mode, g, g32, ph, st, q_in, dq, q_out, s);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_q_from_U_mx(const DevGeom& g, const Physics& ph, const V4* U, QHL* q,
+                               cudaStream_t s) {
+    k_q_from_U_mx<<<grid_for(g.n, 256), 256, 0, s>>>(g, ph, U, q);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dq_to_user_mx(const DevGeom& g, const D8f* src, V8* dst_user, cudaStream_t s) {
+    k_dq_to_v8<<<grid_for(g.n, 256), 256, 0, s>>>(g, src, dst_user);
+    return cudaGetLastError();
+}
+
+}  // namespace lskum

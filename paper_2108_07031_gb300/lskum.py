@@ -27,6 +27,7 @@ ERRORS = {
 
 INTERIOR, WALL, OUTER = 0, 1, 2
 OUTER_KINETIC, OUTER_FREESTREAM = 0, 1
+FP64, MIXED = 0, 1
 KERNEL_FLUX, KERNEL_LS_FIRST, KERNEL_LS_INNER, KERNEL_REDUCE = 0, 1, 2, 3
 
 # every exported entry point of include/lskum.h
