@@ -290,26 +290,61 @@ def run_ours(args, rank, world, local):
         }
     solver.close()
     if args.variants:
-        mixed = time_variant(args, cloud, L.MIXED, stream, barrier, dist)
+        from paper_2108_07031_gb300 import cloud as Cl
+        variants = {"mixed": time_variant(args, cloud, L.MIXED, 1, stream, barrier, dist,
+                                          "10M-point cloud, one condition, block sizes autotuned",
+                                          autotune=True)}
+        c06 = _cloud(600_000)
+        mach, alpha = Cl.conditions(64)
+        variants["batched64_mixed"] = time_variant(
+            args, c06, L.MIXED, 64, stream, barrier, dist,
+            "64 seeded conditions (M ~ U[0.3,0.8], alpha ~ U[-4,6] deg) on the 600,138-point "
+            "cloud, condition-innermost, block size autotuned", conditions=(mach, alpha),
+            autotune=True)
+        variants["batched64_fp64"] = time_variant(
+            args, c06, L.FP64, 64, stream, barrier, dist,
+            "the same 64 conditions in FP64", conditions=(mach, alpha), autotune=True)
+        packed, sizes = _ragged_cloud()
+        variants["ragged16_mixed"] = time_variant(
+            args, packed, L.MIXED, 1, stream, barrier, dist,
+            f"16 clouds of {min(sizes)}-{max(sizes)} points packed into one launch "
+            f"({packed.n} points)", autotune=True)
         if result is not None:
-            result["variants"] = {"mixed": mixed}
-            result["variants"]["mixed"]["speedup_vs_fp64"] = mixed["value"] / value
+            for v in variants.values():
+                v["speedup_vs_fp64"] = v["value"] / value
+            result["variants"] = variants
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
     return result
 
 
-def time_variant(args, cloud, precision, stream, barrier, dist):
-    """Same timed region as the headline for another precision mode."""
+def _ragged_cloud():
+    from paper_2108_07031_gb300 import cloud as Cl
+    sizes = Cl.ragged_sizes(16)
+    members = [_cloud(n) for n in sizes]
+    packed, _ = Cl.pack(members)
+    return packed, [m.n for m in members]
+
+
+def time_variant(args, cloud, precision, n_cond, stream, barrier, dist, what,
+                 conditions=None, autotune=False):
+    """Same timed region as the headline for another precision / batch shape."""
     import torch
 
     from paper_2108_07031_gb300 import cloud as Cl
     from paper_2108_07031_gb300 import lskum as L
-    s = L.Solver.from_cloud(cloud, precision=precision)
+    s = L.Solver.from_cloud(cloud, precision=precision, n_conditions=n_cond)
     s.set_stream(stream.cuda_stream)
-    s.set_freestream(MACH, ALPHA)
-    s.set_state(Cl.perturbed_state(cloud, MACH, ALPHA))
+    if conditions is None:
+        s.set_freestream(MACH, ALPHA)
+        W = Cl.perturbed_state(cloud, MACH, ALPHA)
+    else:
+        s.set_conditions(*conditions)
+        W = np.stack([Cl.perturbed_state(cloud, m, a) for m, a in zip(*conditions)])
+    s.set_state(W)
+    del W
+    block = list(s.autotune(1)) if autotune else [128, 128]
     s.step(args.warmup)
     s.profile(True)
     start = torch.cuda.Event(enable_timing=True)
@@ -334,11 +369,12 @@ def time_variant(args, cloud, precision, stream, barrier, dist):
         t = torch.tensor([ms], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         t_max = float(t.item())
-    value = world * cloud.n * args.steps / (t_max * 1e-3)
-    return {"precision": "mixed" if precision == L.MIXED else "fp64", "value": value,
-            "unit": UNIT, "ms_per_step": t_max / args.steps, "gpu_launches": int(launches),
-            "kernel_ms": {k: {"total_ms": v[0], "launches": v[1]} for k, v in kt.items()},
-            "dtype": "f32 flux/LS arithmetic, f64 state/residue/forces"}
+    value = world * cloud.n * n_cond * args.steps / (t_max * 1e-3)
+    return {"workload": what, "precision": "mixed" if precision == L.MIXED else "fp64",
+            "points": cloud.n, "conditions": n_cond, "block_size": {"flux": block[0], "q_derivatives": block[1]},
+            "value": value, "unit": "point-condition-iterations/s" if n_cond > 1 else UNIT,
+            "ms_per_step": t_max / args.steps, "gpu_launches": int(launches),
+            "kernel_ms": {k: {"total_ms": v[0], "launches": v[1]} for k, v in kt.items()}}
 
 
 def _oracle_sample_rate(iters: int):

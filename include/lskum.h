@@ -80,6 +80,11 @@ typedef struct {
     int reorder;        /* 1: Hilbert-curve point order on the device (default); 0: input order */
     int block_size;     /* CUDA threads per block of the point kernels; 0 = library default */
     int check_every;    /* lskum_solve: iterations between host convergence checks; default 50 */
+    int n_conditions;   /* free streams solved together on the same cloud (a power of two,
+                           1..256; default 1). State is laid out condition-innermost on the
+                           device; every per-point host array below then holds n_conditions
+                           blocks of n points (condition-major), and per-run outputs
+                           (residue, Cl, Cd) hold n_conditions values. */
 } lskum_options;
 
 /* Fills *o with the defaults listed above. Returns LSKUM_ERR_INVALID_ARG if o is NULL. */
@@ -115,14 +120,20 @@ int lskum_set_stream(lskum_ctx* ctx, void* stream);
 
 /* Free stream rho = 1, p = 1/gamma, u = mach (cos a, sin a), alpha in degrees;
  * also resets the state to the free stream everywhere (the initial condition)
- * and clears the residue history. */
+ * and clears the residue history. With n_conditions > 1 every condition gets
+ * this free stream. */
 int lskum_set_freestream(lskum_ctx* ctx, double mach, double alpha_deg);
 
-/* Sets the state from n x 4 primitive values (caller's order, host).
+/* One free stream per condition (mach[k], alpha_deg[k], k < n_cond; n_cond
+ * must equal the context's n_conditions); resets every condition's state to
+ * its free stream and clears the residue history. */
+int lskum_set_conditions(lskum_ctx* ctx, int n_cond, const double* mach, const double* alpha_deg);
+
+/* Sets the state from n_conditions x n x 4 primitive values (caller's order, host).
  * Errors: INVALID_ARG (null), DIVERGED (non-positive rho or p, non-finite). */
 int lskum_set_state(lskum_ctx* ctx, const double* prim);
 
-/* Copies the current primitive state (n x 4, caller's order) to host `prim`. */
+/* Copies the current primitive state (n_conditions x n x 4, caller's order) to host `prim`. */
 int lskum_get_state(lskum_ctx* ctx, double* prim);
 
 /* Runs n_iters pseudo-time iterations of Algorithm 1 on the device (local
@@ -131,31 +142,45 @@ int lskum_get_state(lskum_ctx* ctx, double* prim);
 int lskum_step(lskum_ctx* ctx, int n_iters);
 
 /* Iterates until the residue has dropped by `tol` relative to the first
- * non-zero residue of this run (e.g. tol = 1e-6 for six orders), or
- * max_iters iterations; *iters_done (may be NULL) receives the count. */
+ * non-zero residue of this run (e.g. tol = 1e-6 for six orders) for every
+ * condition, or max_iters iterations; *iters_done (may be NULL) receives the
+ * count. */
 int lskum_solve(lskum_ctx* ctx, int max_iters, double tol, int* iters_done);
 
 /* Residue of the last iteration: sqrt(sum_i R_rho,i^2) / N of its stage-1
- * residual (Algorithm 1, residue()). 0 before the first iteration. */
+ * residual (Algorithm 1, residue()), one value per condition in out[].
+ * 0 before the first iteration. */
 int lskum_residual_norm(lskum_ctx* ctx, double* out);
 
 /* Lift and drag coefficients of the pressure force on the wall loops:
  * F = -sum (p_i - p_inf) n_i ds_i, Cl/Cd in the free-stream axes, chord 1,
- * q_inf = M^2 / 2. */
+ * q_inf = M^2 / 2; one value per condition in cl[], cd[]. */
 int lskum_forces(lskum_ctx* ctx, double* cl, double* cd);
 
 /* Residual R(W) of the current state without updating it: q-variables,
  * q-derivatives (with inner iterations) and flux residual (Eq. 12), written
- * as n x 4 conserved components in the global frame, caller's order. */
+ * as n_conditions x n x 4 conserved components in the global frame, caller's
+ * order. */
 int lskum_eval_residual(lskum_ctx* ctx, double* R);
 
 /* q-derivatives (Eq. 11 followed by inner_iters sweeps of Eq. 29) of the
- * current state: qx, qy are n x 4 each, caller's order. */
+ * current state: qx, qy are n_conditions x n x 4 each, caller's order. */
 int lskum_eval_q_derivatives(lskum_ctx* ctx, double* qx, double* qy);
 
-/* Number of points, of wall points in the force loops, and the neighbour
- * slots per point of the device layout (diagnostics). */
-int lskum_info(lskum_ctx* ctx, int64_t* n_points, int64_t* n_wall, int* max_neighbours);
+/* Number of points, of wall points in the force loops, the neighbour slots
+ * per point of the device layout and the number of conditions (diagnostics;
+ * any pointer may be NULL). */
+int lskum_info(lskum_ctx* ctx, int64_t* n_points, int64_t* n_wall, int* max_neighbours,
+               int* n_conditions);
+
+/* Autotuner: times trial_iters iterations for every pair of thread-block
+ * sizes the library is built for (128, 256), one for the flux/update kernel
+ * and one for the q-derivative kernels, each from the current state; restores
+ * the state, keeps the fastest pair for all later work (re-capturing the
+ * iteration graph) and returns it in *best_block as
+ * flux_block * 1000 + derivative_block (may be NULL). Clears the residue
+ * history. Uses a temporary device buffer of the state's size. */
+int lskum_autotune(lskum_ctx* ctx, int trial_iters, int* best_block);
 
 /* Kernel timing with CUDA events on the context's stream, for the roofline
  * report. lskum_profile(ctx, 1) starts recording (clearing old totals), 0

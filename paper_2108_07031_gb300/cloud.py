@@ -313,6 +313,41 @@ def _shuffle(cloud: Cloud, seed: int) -> Cloud:
                  l=cloud.l[perm].copy())
 
 
+def pack(clouds) -> tuple[Cloud, np.ndarray]:
+    """Concatenate clouds into one (disconnected) cloud for a ragged batch.
+
+    Returns the packed cloud and the point offset of every member (length
+    len(clouds) + 1). Each member's wall loop stays contiguous and first in
+    its block, so the loops stay separate; neighbour lists keep their order.
+    """
+    clouds = list(clouds)
+    offs = np.zeros(len(clouds) + 1, dtype=np.int64)
+    for i, c in enumerate(clouds):
+        offs[i + 1] = offs[i] + c.n
+    nnz = [int(c.nbr_offsets[-1]) for c in clouds]
+    if sum(nnz) > np.iinfo(np.int32).max or offs[-1] > np.iinfo(np.int32).max:
+        raise ValueError("packed cloud too large for int32 connectivity")
+    nbr_off = [np.zeros(1, dtype=np.int64)]
+    base = 0
+    for c in clouds:
+        nbr_off.append(c.nbr_offsets[1:].astype(np.int64) + base)
+        base += int(c.nbr_offsets[-1])
+    idx = np.concatenate([c.nbr_idx.astype(np.int64) + o for c, o in zip(clouds, offs[:-1])])
+    packed = Cloud(xy=np.concatenate([c.xy for c in clouds]),
+                   normals=np.concatenate([c.normals for c in clouds]),
+                   flags=np.concatenate([c.flags for c in clouds]),
+                   nbr_offsets=np.concatenate(nbr_off).astype(np.int32),
+                   nbr_idx=idx.astype(np.int32), n_c=clouds[0].n_c, n_r=clouds[0].n_r,
+                   k=np.concatenate([c.k for c in clouds]), l=np.concatenate([c.l for c in clouds]))
+    return packed, offs
+
+
+def ragged_sizes(n_clouds: int = 16, lo: int = 100_000, hi: int = 1_000_000, seed: int = 2021):
+    """Seeded cloud sizes ~ U[lo, hi] for a ragged batch."""
+    rng = np.random.Generator(np.random.PCG64(seed + 7))
+    return [int(v) for v in rng.uniform(lo, hi, n_clouds)]
+
+
 def cloud_for_points(n_points: int, seed: int = 12345, shuffle: bool = True) -> Cloud:
     """The cloud whose size is closest to ``n_points`` (same continuous distribution)."""
     n_c, n_r = cloud_dims(n_points)

@@ -42,7 +42,8 @@ struct lskum_ctx {
     int device = 0;
     cudaStream_t own_stream = nullptr;
     cudaStream_t stream = nullptr;
-    int block = kDefaultBlock;
+    int block = kDefaultBlock;     // flux / update kernel
+    int block_ls = kDefaultBlock;  // q-derivative kernels
 
     HostLayout host;
     bool mixed = false;
@@ -52,13 +53,15 @@ struct lskum_ctx {
     DevState st{};
     std::vector<void*> allocations;
 
-    V4* staging = nullptr;  // n x 4 in caller order (state transfer)
-    V8* staging8 = nullptr; // n x 8 in caller order (derivative output)
+    V4* staging = nullptr;  // C x n x 4 in caller order (state transfer)
+    V8* staging8 = nullptr; // C x n x 8 in caller order (derivative output)
     int* h_status = nullptr;             // pinned
     double* h_small = nullptr;           // pinned scratch for small reads
 
     bool have_state = false;
-    double mach = 0.0, alpha = 0.0;
+    int C = 1;                       // conditions solved together
+    std::vector<double> mach, alpha; // free stream per condition
+    V4* w_cond = nullptr;            // device copy of the free streams
     int64_t iters_done = 0;  // iterations since the last state reset
 
     cudaGraph_t graph = nullptr;
@@ -140,8 +143,8 @@ int n_blocks(const lskum_ctx* c) { return int((c->g.n + c->block - 1) / c->block
 // (mixed); returns the index of the buffer holding the result.
 cudaError_t run_q_derivatives(lskum_ctx* c, int qb, int* final_buf, int64_t* launches) {
     cudaError_t e = timed(c, kLsFirst, [&] {
-        return c->mixed ? launch_ls_first_mx(c->g, c->g32, c->st.qhl[qb], c->st.dq32[0], c->block, c->stream)
-                        : launch_ls_first(c->g, c->st.q[qb], c->st.dq[0], c->block, c->stream);
+        return c->mixed ? launch_ls_first_mx(c->g, c->g32, c->st.qhl[qb], c->st.dq32[0], c->block_ls, c->stream)
+                        : launch_ls_first(c->g, c->st.q[qb], c->st.dq[0], c->block_ls, c->stream);
     });
     if (e != cudaSuccess) return e;
     ++*launches;
@@ -149,9 +152,9 @@ cudaError_t run_q_derivatives(lskum_ctx* c, int qb, int* final_buf, int64_t* lau
     for (int it = 0; it < c->opt.inner_iters; ++it) {
         e = timed(c, kLsInner, [&] {
             return c->mixed ? launch_ls_inner_mx(c->g, c->g32, c->st.qhl[qb], c->st.dq32[cur],
-                                                 c->st.dq32[1 - cur], c->block, c->stream)
+                                                 c->st.dq32[1 - cur], c->block_ls, c->stream)
                             : launch_ls_inner(c->g, c->st.q[qb], c->st.dq[cur], c->st.dq[1 - cur],
-                                              c->block, c->stream);
+                                              c->block_ls, c->stream);
         });
         if (e != cudaSuccess) return e;
         ++*launches;
@@ -182,12 +185,24 @@ cudaError_t run_iteration(lskum_ctx* c, int64_t* launches) {
         ++*launches;
         qcur = 1 - qcur;
         if (stage == 1) {
-            e = timed(c, kReduce, [&] { return launch_residue(c->st, n_blocks(c), c->g.n, c->stream); });
+            e = timed(c, kReduce, [&] {
+                return c->C == 1 ? launch_residue(c->st, n_blocks(c), c->g.n, c->stream)
+                                 : launch_residue_cond(c->g, c->st, c->stream);
+            });
             if (e != cudaSuccess) return e;
-            ++*launches;
+            *launches += c->C == 1 ? 1 : 2;
         }
     }
     return cudaSuccess;
+}
+
+cudaError_t refresh_mixed_q(lskum_ctx* c);
+
+// q-variables of the current U in both representations.
+cudaError_t launch_q_refresh(lskum_ctx* c) {
+    cudaError_t e = launch_q_from_U(c->g, c->ph, c->st.U, c->st.q[0], c->stream);
+    if (e != cudaSuccess) return e;
+    return refresh_mixed_q(c);
 }
 
 // After U changed from the host side: the mixed path's float-pair q.
@@ -210,12 +225,14 @@ int read_status(lskum_ctx* c, int* status) {
     return LSKUM_OK;
 }
 
+// Residues of iteration `iter` (0-based since the last reset), one per
+// condition, into out[C].
 int read_residue(lskum_ctx* c, int64_t iter, double* out) {
-    const int64_t slot = iter % kResCap;
-    LSKUM_CUDA(cudaMemcpyAsync(c->h_small, c->st.res_hist + slot, sizeof(double),
+    const int64_t slot = iter % (kResCap / c->C);
+    LSKUM_CUDA(cudaMemcpyAsync(c->h_small, c->st.res_hist + slot * c->C, sizeof(double) * c->C,
                                cudaMemcpyDeviceToHost, c->stream));
     LSKUM_CUDA(cudaStreamSynchronize(c->stream));
-    *out = *c->h_small;
+    for (int k = 0; k < c->C; ++k) out[k] = c->h_small[k];
     return LSKUM_OK;
 }
 
@@ -235,6 +252,7 @@ int lskum_default_options(lskum_options* o) {
     o->reorder = 1;
     o->block_size = 0;
     o->check_every = 50;
+    o->n_conditions = 1;
     return LSKUM_OK;
 }
 
@@ -250,14 +268,19 @@ int lskum_create(int64_t n, const double* xy, const double* normals, const int8_
         o.inner_iters > 64 || (o.order != 1 && o.order != 2) || !(o.wall_factor > 0.0) ||
         (o.outer_mode != 0 && o.outer_mode != 1) ||
         (o.precision != LSKUM_FP64 && o.precision != LSKUM_MIXED) ||
-        (o.block_size != 0 && o.block_size != 128 && o.block_size != 256) || o.check_every < 1)
+        (o.block_size != 0 && o.block_size != 128 && o.block_size != 256) || o.check_every < 1 ||
+        o.n_conditions < 1 || o.n_conditions > 256 || (o.n_conditions & (o.n_conditions - 1)))
         return fail(LSKUM_ERR_INVALID_ARG, "invalid option value");
 
     lskum_ctx* c = new (std::nothrow) lskum_ctx();
     if (!c) return fail(LSKUM_ERR_INVALID_ARG, "out of host memory");
     c->opt = o;
     c->block = o.block_size ? o.block_size : kDefaultBlock;
+    c->block_ls = c->block;
     c->mixed = o.precision == LSKUM_MIXED;
+    c->C = o.n_conditions;
+    c->mach.assign(c->C, 0.0);
+    c->alpha.assign(c->C, 0.0);
 
     // host validation and layout first: input errors are reported without a GPU
     std::string err;
@@ -290,6 +313,9 @@ int lskum_create(int64_t n, const double* xy, const double* normals, const int8_
     g.stride = L.stride;
     g.slots = L.slots;
     g.n_wall = int64_t(L.wall_id.size());
+    g.cshift = 0;
+    while ((1 << g.cshift) < c->C) ++g.cshift;
+    g.cmask = uint32_t(c->C - 1);
     std::vector<double2> nrm2(L.n), nds2(L.wall_id.size());
     for (int64_t i = 0; i < L.n; ++i) nrm2[i] = make_double2(L.nrm[2 * i], L.nrm[2 * i + 1]);
     for (size_t k = 0; k < L.wall_id.size(); ++k) nds2[k] = make_double2(L.wall_nds[2 * k], L.wall_nds[2 * k + 1]);
@@ -324,8 +350,8 @@ int lskum_create(int64_t n, const double* xy, const double* normals, const int8_
     }
 
     DevState& st = c->st;
-    const size_t N = size_t(L.n);
-    const int nb = int((L.n + 127) / 128) + 1;  // enough for either block size
+    const size_t N = size_t(L.n) * size_t(c->C);  // (point, condition) pairs
+    const int nb = int((L.n + 127) / 128) + 1;  // block partials when C == 1
     if (c->mixed) {
         if ((e = dev_alloc(c, &st.qhl[0], N)) != cudaSuccess ||
             (e = dev_alloc(c, &st.qhl[1], N)) != cudaSuccess ||
@@ -345,12 +371,17 @@ int lskum_create(int64_t n, const double* xy, const double* normals, const int8_
         (e = dev_alloc(c, &st.res_hist, size_t(kResCap))) != cudaSuccess ||
         (e = dev_alloc(c, &st.iter_counter, 1)) != cudaSuccess ||
         (e = dev_alloc(c, &st.status, 1)) != cudaSuccess ||
-        (e = dev_alloc(c, &st.force_out, 2)) != cudaSuccess ||
+        (e = dev_alloc(c, &st.force_out, size_t(2 * c->C))) != cudaSuccess ||
+        (e = dev_alloc(c, &c->w_cond, size_t(c->C))) != cudaSuccess ||
         (e = dev_alloc(c, &c->staging, N)) != cudaSuccess)
         return bail(e, "device state allocation");
+    if (c->C > 1 &&
+        ((e = dev_alloc(c, &st.r2, N)) != cudaSuccess ||
+         (e = dev_alloc(c, &st.cpartials, size_t(kCondReduceBlocks) * c->C)) != cudaSuccess))
+        return bail(e, "per-condition residue scratch");
     st.res_cap = kResCap;
     if ((e = cudaMallocHost(&c->h_status, sizeof(int) * 4)) != cudaSuccess ||
-        (e = cudaMallocHost(&c->h_small, sizeof(double) * 4)) != cudaSuccess)
+        (e = cudaMallocHost(&c->h_small, sizeof(double) * size_t(std::max(4, 2 * c->C)))) != cudaSuccess)
         return bail(e, "pinned host allocation");
 
     Physics& ph = c->ph;
@@ -384,25 +415,42 @@ int lskum_set_stream(lskum_ctx* c, void* stream) {
     return LSKUM_OK;
 }
 
-int lskum_set_freestream(lskum_ctx* c, double mach, double alpha_deg) {
-    if (!c) return fail(LSKUM_ERR_INVALID_ARG, "null context");
-    if (!(mach >= 0.0) || !std::isfinite(mach) || !std::isfinite(alpha_deg))
-        return fail(LSKUM_ERR_INVALID_ARG, "invalid free stream");
-    c->mach = mach;
-    c->alpha = alpha_deg;
-    const double a = alpha_deg * kPi / 180.0;
-    const V4 W{1.0, mach * std::cos(a), mach * std::sin(a), 1.0 / c->opt.gamma};
-    LSKUM_CUDA(launch_set_uniform(c->g, c->ph, W, c->st.U, c->st.q[0], c->stream));
+int lskum_set_conditions(lskum_ctx* c, int n_cond, const double* mach, const double* alpha_deg) {
+    if (!c || !mach || !alpha_deg) return fail(LSKUM_ERR_INVALID_ARG, "null argument");
+    if (n_cond != c->C)
+        return fail(LSKUM_ERR_INVALID_ARG, "n_cond = " + std::to_string(n_cond) +
+                                               " differs from the context's n_conditions = " +
+                                               std::to_string(c->C));
+    std::vector<V4> W(c->C);
+    for (int k = 0; k < c->C; ++k) {
+        if (!(mach[k] >= 0.0) || !std::isfinite(mach[k]) || !std::isfinite(alpha_deg[k]))
+            return fail(LSKUM_ERR_INVALID_ARG, "invalid free stream");
+        const double a = alpha_deg[k] * kPi / 180.0;
+        W[k] = V4{1.0, mach[k] * std::cos(a), mach[k] * std::sin(a), 1.0 / c->opt.gamma};
+    }
+    LSKUM_CUDA(cudaMemcpyAsync(c->w_cond, W.data(), sizeof(V4) * W.size(), cudaMemcpyHostToDevice,
+                               c->stream));
+    LSKUM_CUDA(launch_set_uniform(c->g, c->ph, c->w_cond, c->st.U, c->st.q[0], c->stream));
     LSKUM_CUDA(refresh_mixed_q(c));
     int rc = reset_history(c);
     if (rc != LSKUM_OK) return rc;
+    LSKUM_CUDA(cudaStreamSynchronize(c->stream));  // W is a pageable host buffer
+    c->mach.assign(mach, mach + c->C);
+    c->alpha.assign(alpha_deg, alpha_deg + c->C);
     c->have_state = true;
     return LSKUM_OK;
 }
 
+int lskum_set_freestream(lskum_ctx* c, double mach, double alpha_deg) {
+    if (!c) return fail(LSKUM_ERR_INVALID_ARG, "null context");
+    std::vector<double> m(c->C, mach), a(c->C, alpha_deg);
+    return lskum_set_conditions(c, c->C, m.data(), a.data());
+}
+
 int lskum_set_state(lskum_ctx* c, const double* prim) {
     if (!c || !prim) return fail(LSKUM_ERR_INVALID_ARG, "null argument");
-    LSKUM_CUDA(cudaMemcpyAsync(c->staging, prim, sizeof(V4) * size_t(c->g.n), cudaMemcpyHostToDevice, c->stream));
+    LSKUM_CUDA(cudaMemcpyAsync(c->staging, prim, sizeof(V4) * size_t(c->g.n) * c->C,
+                               cudaMemcpyHostToDevice, c->stream));
     int rc = reset_history(c);
     if (rc != LSKUM_OK) return rc;
     LSKUM_CUDA(launch_set_prim(c->g, c->ph, c->staging, c->st.U, c->st.q[0], c->st.status, c->stream));
@@ -423,7 +471,8 @@ int lskum_get_state(lskum_ctx* c, double* prim) {
     if (!c || !prim) return fail(LSKUM_ERR_INVALID_ARG, "null argument");
     if (!c->have_state) return fail(LSKUM_ERR_STATE, "no state set");
     LSKUM_CUDA(launch_get_prim(c->g, c->ph, c->st.U, c->staging, c->stream));
-    LSKUM_CUDA(cudaMemcpyAsync(prim, c->staging, sizeof(V4) * size_t(c->g.n), cudaMemcpyDeviceToHost, c->stream));
+    LSKUM_CUDA(cudaMemcpyAsync(prim, c->staging, sizeof(V4) * size_t(c->g.n) * c->C,
+                               cudaMemcpyDeviceToHost, c->stream));
     LSKUM_CUDA(cudaStreamSynchronize(c->stream));
     return LSKUM_OK;
 }
@@ -447,7 +496,7 @@ int lskum_step(lskum_ctx* c, int n_iters) {
     for (int it = 0; it < n_iters; ++it) {
         if (graph) {
             LSKUM_CUDA(cudaGraphLaunch(c->graph_exec, c->stream));
-            launches += 4 * (2 + c->opt.inner_iters) + 1;
+            launches += 4 * (2 + c->opt.inner_iters) + (c->C == 1 ? 1 : 2);
         } else {
             cudaError_t e = run_iteration(c, &launches);
             if (e != cudaSuccess) return cuda_fail(e, "iteration launch");
@@ -466,28 +515,31 @@ int lskum_solve(lskum_ctx* c, int max_iters, double tol, int* iters_done) {
     if (!c || max_iters < 0 || !(tol > 0.0)) return fail(LSKUM_ERR_INVALID_ARG, "invalid argument");
     if (iters_done) *iters_done = 0;
     int done = 0;
-    double first = 0.0;
-    int64_t first_iter = c->iters_done;
+    const int C = c->C;
+    std::vector<double> first(C, 0.0), r(C, 0.0);
+    int64_t scan_from = c->iters_done;
     while (done < max_iters) {
         const int chunk = std::min(c->opt.check_every, max_iters - done);
         int rc = lskum_step(c, chunk);
         done += chunk;
         if (iters_done) *iters_done = done;
         if (rc != LSKUM_OK) return rc;
-        if (first == 0.0) {
-            // first non-zero residue of this run
-            for (int64_t k = first_iter; k < c->iters_done && first == 0.0; ++k) {
-                double r = 0.0;
-                rc = read_residue(c, k, &r);
-                if (rc != LSKUM_OK) return rc;
-                if (r > 0.0) first = r;
-            }
-            first_iter = c->iters_done;
+        // first non-zero residue of this run, per condition
+        for (int64_t k = scan_from; k < c->iters_done; ++k) {
+            bool all = true;
+            for (int m = 0; m < C; ++m) all = all && first[m] > 0.0;
+            if (all) break;
+            rc = read_residue(c, k, r.data());
+            if (rc != LSKUM_OK) return rc;
+            for (int m = 0; m < C; ++m)
+                if (first[m] == 0.0 && r[m] > 0.0) first[m] = r[m];
         }
-        double last = 0.0;
-        rc = read_residue(c, c->iters_done - 1, &last);
+        scan_from = c->iters_done;
+        rc = read_residue(c, c->iters_done - 1, r.data());
         if (rc != LSKUM_OK) return rc;
-        if (first > 0.0 && last <= tol * first) break;
+        bool converged = true;
+        for (int m = 0; m < C; ++m) converged = converged && first[m] > 0.0 && r[m] <= tol * first[m];
+        if (converged) break;
     }
     return LSKUM_OK;
 }
@@ -495,7 +547,7 @@ int lskum_solve(lskum_ctx* c, int max_iters, double tol, int* iters_done) {
 int lskum_residual_norm(lskum_ctx* c, double* out) {
     if (!c || !out) return fail(LSKUM_ERR_INVALID_ARG, "null argument");
     if (c->iters_done == 0) {
-        *out = 0.0;
+        for (int k = 0; k < c->C; ++k) out[k] = 0.0;
         return LSKUM_OK;
     }
     return read_residue(c, c->iters_done - 1, out);
@@ -505,14 +557,17 @@ int lskum_forces(lskum_ctx* c, double* cl, double* cd) {
     if (!c || !cl || !cd) return fail(LSKUM_ERR_INVALID_ARG, "null argument");
     if (!c->have_state) return fail(LSKUM_ERR_STATE, "no state set");
     LSKUM_CUDA(launch_forces(c->g, c->ph, c->st, c->stream));
-    LSKUM_CUDA(cudaMemcpyAsync(c->h_small, c->st.force_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    LSKUM_CUDA(cudaMemcpyAsync(c->h_small, c->st.force_out, 2 * sizeof(double) * c->C,
+                               cudaMemcpyDeviceToHost, c->stream));
     LSKUM_CUDA(cudaStreamSynchronize(c->stream));
-    const double fx = c->h_small[0], fy = c->h_small[1];
-    const double a = c->alpha * kPi / 180.0;
-    const double qinf = 0.5 * c->mach * c->mach;
-    if (!(qinf > 0.0)) return fail(LSKUM_ERR_STATE, "forces need a free stream with M > 0");
-    *cl = (-fx * std::sin(a) + fy * std::cos(a)) / qinf;
-    *cd = (fx * std::cos(a) + fy * std::sin(a)) / qinf;
+    for (int k = 0; k < c->C; ++k) {
+        const double fx = c->h_small[2 * k], fy = c->h_small[2 * k + 1];
+        const double a = c->alpha[k] * kPi / 180.0;
+        const double qinf = 0.5 * c->mach[k] * c->mach[k];
+        if (!(qinf > 0.0)) return fail(LSKUM_ERR_STATE, "forces need a free stream with M > 0");
+        cl[k] = (-fx * std::sin(a) + fy * std::cos(a)) / qinf;
+        cd[k] = (fx * std::cos(a) + fy * std::sin(a)) / qinf;
+    }
     return LSKUM_OK;
 }
 
@@ -525,7 +580,8 @@ int lskum_eval_residual(lskum_ctx* c, double* R) {
     if (e != cudaSuccess) return cuda_fail(e, "q-derivatives");
     LSKUM_CUDA(launch_flux_any(c, 0, 0, dbuf, -1));
     LSKUM_CUDA(launch_gather_v4(c->g, c->st.R, c->staging, c->stream));
-    LSKUM_CUDA(cudaMemcpyAsync(R, c->staging, sizeof(V4) * size_t(c->g.n), cudaMemcpyDeviceToHost, c->stream));
+    LSKUM_CUDA(cudaMemcpyAsync(R, c->staging, sizeof(V4) * size_t(c->g.n) * c->C,
+                               cudaMemcpyDeviceToHost, c->stream));
     LSKUM_CUDA(cudaStreamSynchronize(c->stream));
     return LSKUM_OK;
 }
@@ -534,7 +590,7 @@ int lskum_eval_q_derivatives(lskum_ctx* c, double* qx, double* qy) {
     if (!c || !qx || !qy) return fail(LSKUM_ERR_INVALID_ARG, "null argument");
     if (!c->have_state) return fail(LSKUM_ERR_STATE, "no state set");
     if (!c->staging8) {
-        LSKUM_CUDA(dev_alloc(c, &c->staging8, size_t(c->g.n)));
+        LSKUM_CUDA(dev_alloc(c, &c->staging8, size_t(c->g.n) * c->C));
     }
     int dbuf = 0;
     int64_t launches = 0;
@@ -545,7 +601,7 @@ int lskum_eval_q_derivatives(lskum_ctx* c, double* qx, double* qy) {
     } else {
         LSKUM_CUDA(launch_gather_v8(c->g, c->st.dq[dbuf], c->staging8, c->stream));
     }
-    std::vector<V8> h(size_t(c->g.n));
+    std::vector<V8> h(size_t(c->g.n) * c->C);
     LSKUM_CUDA(cudaMemcpyAsync(h.data(), c->staging8, sizeof(V8) * h.size(), cudaMemcpyDeviceToHost, c->stream));
     LSKUM_CUDA(cudaStreamSynchronize(c->stream));
     for (size_t i = 0; i < h.size(); ++i)
@@ -556,11 +612,79 @@ int lskum_eval_q_derivatives(lskum_ctx* c, double* qx, double* qy) {
     return LSKUM_OK;
 }
 
-int lskum_info(lskum_ctx* c, int64_t* n_points, int64_t* n_wall, int* max_neighbours) {
+int lskum_info(lskum_ctx* c, int64_t* n_points, int64_t* n_wall, int* max_neighbours,
+               int* n_conditions) {
     if (!c) return fail(LSKUM_ERR_INVALID_ARG, "null context");
     if (n_points) *n_points = c->g.n;
     if (n_wall) *n_wall = c->g.n_wall;
     if (max_neighbours) *max_neighbours = c->g.slots;
+    if (n_conditions) *n_conditions = c->C;
+    return LSKUM_OK;
+}
+
+int lskum_autotune(lskum_ctx* c, int trial_iters, int* best_block) {
+    if (!c || trial_iters < 1) return fail(LSKUM_ERR_INVALID_ARG, "invalid argument");
+    if (!c->have_state) return fail(LSKUM_ERR_STATE, "no state set");
+    // keep the state: every trial restarts from it
+    V4* saved = nullptr;
+    const size_t N = size_t(c->g.n) * c->C;
+    LSKUM_CUDA(cudaMalloc(&saved, sizeof(V4) * N));
+    LSKUM_CUDA(cudaMemcpyAsync(saved, c->st.U, sizeof(V4) * N, cudaMemcpyDeviceToDevice, c->stream));
+    const int candidates[2] = {128, 256};
+    double best_ms = 1e300;
+    int best = c->block, best_ls = c->block_ls;
+    cudaEvent_t e0, e1;
+    LSKUM_CUDA(cudaEventCreate(&e0));
+    LSKUM_CUDA(cudaEventCreate(&e1));
+    const bool was_profiling = c->profiling;
+    c->profiling = false;
+    for (int cand : candidates) {
+        for (int cand_ls : candidates) {
+            c->block = cand;
+            c->block_ls = cand_ls;
+            int64_t launches = 0;
+            cudaError_t e = run_iteration(c, &launches);  // warm-up of this shape
+            if (e != cudaSuccess) return cuda_fail(e, "autotune warm-up");
+            LSKUM_CUDA(cudaEventRecord(e0, c->stream));
+            for (int k = 0; k < trial_iters; ++k) {
+                e = run_iteration(c, &launches);
+                if (e != cudaSuccess) return cuda_fail(e, "autotune trial");
+            }
+            LSKUM_CUDA(cudaEventRecord(e1, c->stream));
+            LSKUM_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            LSKUM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = cand;
+                best_ls = cand_ls;
+            }
+            LSKUM_CUDA(cudaMemcpyAsync(c->st.U, saved, sizeof(V4) * N, cudaMemcpyDeviceToDevice,
+                                       c->stream));
+        }
+    }
+    c->profiling = was_profiling;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    LSKUM_CUDA(cudaStreamSynchronize(c->stream));
+    cudaFree(saved);
+    c->block = best;
+    c->block_ls = best_ls;
+    // the state is back to where it was: rebuild q, drop the captured graph
+    // (its launch shapes belong to the old block size) and the trial history
+    LSKUM_CUDA(launch_q_refresh(c));
+    if (c->graph_exec) {
+        cudaGraphExecDestroy(c->graph_exec);
+        c->graph_exec = nullptr;
+    }
+    if (c->graph) {
+        cudaGraphDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    int rc = reset_history(c);
+    if (rc != LSKUM_OK) return rc;
+    LSKUM_CUDA(cudaStreamSynchronize(c->stream));
+    if (best_block) *best_block = best * 1000 + best_ls;
     return LSKUM_OK;
 }
 

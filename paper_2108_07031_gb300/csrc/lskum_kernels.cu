@@ -152,16 +152,18 @@ __device__ __forceinline__ double block_sum(double x) {
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK) k_ls_first(const DevGeom g, const V4* __restrict__ q,
                                                     V8* __restrict__ dq) {
-    const int64_t d = int64_t(blockIdx.x) * BLOCK + threadIdx.x;
+    const int64_t t = int64_t(blockIdx.x) * BLOCK + threadIdx.x;  // (point, condition)
+    const int64_t d = t >> g.cshift;
+    const uint32_t cc = uint32_t(t) & g.cmask;
     if (d >= g.n) return;
-    const V4 qi = ld4(q + d);
+    const V4 qi = ld4(q + t);
     double ax[4] = {0, 0, 0, 0}, ay[4] = {0, 0, 0, 0};
     const int c = g.cnt[d];
     for (int k = 0; k < c; ++k) {
         const int64_t at = int64_t(k) * g.stride + d;
         const uint32_t j = g.nbr[at] & kIndexMask;
         const double wx = g.wx[at], wy = g.wy[at];
-        const V4 qj = ld4(q + j);
+        const V4 qj = ld4(q + sidx(g, j, cc));
         const double dq0 = qj.a - qi.a, dq1 = qj.b - qi.b, dq2 = qj.c - qi.c, dq3 = qj.d - qi.d;
         ax[0] += wx * dq0; ax[1] += wx * dq1; ax[2] += wx * dq2; ax[3] += wx * dq3;
         ay[0] += wy * dq0; ay[1] += wy * dq1; ay[2] += wy * dq2; ay[3] += wy * dq3;
@@ -172,17 +174,19 @@ __global__ void __launch_bounds__(BLOCK) k_ls_first(const DevGeom g, const V4* _
         o.x[m] = ax[m];
         o.y[m] = ay[m];
     }
-    dq[d] = o;
+    dq[t] = o;
 }
 
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK) k_ls_inner(const DevGeom g, const V4* __restrict__ q,
                                                     const V8* __restrict__ din,
                                                     V8* __restrict__ dout) {
-    const int64_t d = int64_t(blockIdx.x) * BLOCK + threadIdx.x;
+    const int64_t t = int64_t(blockIdx.x) * BLOCK + threadIdx.x;  // (point, condition)
+    const int64_t d = t >> g.cshift;
+    const uint32_t cc = uint32_t(t) & g.cmask;
     if (d >= g.n) return;
-    const V4 qi = ld4(q + d);
-    const V8 di = din[d];
+    const V4 qi = ld4(q + t);
+    const V8 di = din[t];
     const double qiv[4] = {qi.a, qi.b, qi.c, qi.d};
     double ax[4] = {0, 0, 0, 0}, ay[4] = {0, 0, 0, 0};
     const int c = g.cnt[d];
@@ -191,8 +195,9 @@ __global__ void __launch_bounds__(BLOCK) k_ls_inner(const DevGeom g, const V4* _
         const uint32_t j = g.nbr[at] & kIndexMask;
         const double wx = g.wx[at], wy = g.wy[at];
         const double hx = g.hdx[at], hy = g.hdy[at];
-        const V4 qj = ld4(q + j);
-        const V8 dj = din[j];
+        const int64_t tj = sidx(g, j, cc);
+        const V4 qj = ld4(q + tj);
+        const V8 dj = din[tj];
         const double qjv[4] = {qj.a, qj.b, qj.c, qj.d};
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
@@ -208,7 +213,7 @@ __global__ void __launch_bounds__(BLOCK) k_ls_inner(const DevGeom g, const V4* _
         o.x[m] = ax[m];
         o.y[m] = ay[m];
     }
-    dout[d] = o;
+    dout[t] = o;
 }
 
 // ------------------------------------------------------- flux residual + RK
@@ -217,7 +222,9 @@ template <int MODE, int BLOCK, bool G14>
 __global__ void __launch_bounds__(BLOCK) k_flux(const DevGeom g, const Physics ph,
                                                 const DevState st, const V4* __restrict__ q_in,
                                                 const V8* __restrict__ dq, V4* __restrict__ q_out) {
-    const int64_t d = int64_t(blockIdx.x) * BLOCK + threadIdx.x;
+    const int64_t t = int64_t(blockIdx.x) * BLOCK + threadIdx.x;  // (point, condition)
+    const int64_t d = t >> g.cshift;
+    const uint32_t cc = uint32_t(t) & g.cmask;
     double r2 = 0.0;
     if (d < g.n) {
         const int8_t fl = g.flag[d];
@@ -233,8 +240,8 @@ __global__ void __launch_bounds__(BLOCK) k_flux(const DevGeom g, const Physics p
                 tx = ny;
                 ty = -nx;
             }
-            const V4 qi = ld4(q_in + d);
-            const V8 di = dq[d];
+            const V4 qi = ld4(q_in + t);
+            const V8 di = dq[t];
             const double qiv[4] = {qi.a, qi.b, qi.c, qi.d};
             const bool second = ph.order == 2;
             const int c = g.cnt[d];
@@ -244,12 +251,13 @@ __global__ void __launch_bounds__(BLOCK) k_flux(const DevGeom g, const Physics p
                 const uint32_t j = e & kIndexMask;
                 const uint32_t sc = (e >> kIndexBits) & 3u;
                 const uint32_t nc = (e >> (kIndexBits + 2)) & 3u;
-                const V4 qj = ld4(q_in + j);
+                const int64_t jt = sidx(g, j, cc);
+                const V4 qj = ld4(q_in + jt);
                 double tj[4] = {qj.a, qj.b, qj.c, qj.d};
                 double t0[4] = {qiv[0], qiv[1], qiv[2], qiv[3]};
                 if (second) {
                     const double hx = g.hdx[at], hy = g.hdy[at];
-                    const V8 dj = dq[j];
+                    const V8 dj = dq[jt];
 #pragma unroll
                     for (int m = 0; m < 4; ++m) {
                         tj[m] = tj[m] - (hx * dj.x[m] + hy * dj.y[m]);
@@ -298,24 +306,24 @@ __global__ void __launch_bounds__(BLOCK) k_flux(const DevGeom g, const Physics p
             }
         }
         if (MODE == 0) {
-            st.R[d] = V4{R[0], R[1], R[2], R[3]};
+            st.R[t] = V4{R[0], R[1], R[2], R[3]};
         } else {
-            V4 U = ld4(st.U + d);
+            V4 U = ld4(st.U + t);
             double dtv;
             if (MODE == 1) {
                 const double rho = U.a, u = U.b / rho, v = U.c / rho;
                 const double p = ph.gm1 * (U.d - 0.5 * rho * (u * u + v * v));
                 dtv = ph.cfl * g.dmin[d] / (sqrt(u * u + v * v) + sqrt(ph.gamma * p / rho));
-                st.dt[d] = dtv;
-                st.U0[d] = U;
+                st.dt[t] = dtv;
+                st.U0[t] = U;
                 r2 = R[0] * R[0];
             } else {
-                dtv = st.dt[d];
+                dtv = st.dt[t];
             }
             if (!fixed) {
                 const double h = 0.5 * dtv;
                 if (MODE == 3) {
-                    const V4 U0 = ld4(st.U0 + d);
+                    const V4 U0 = ld4(st.U0 + t);
                     U.a = (2.0 / 3.0) * U0.a + (1.0 / 3.0) * (U.a - h * R[0]);
                     U.b = (2.0 / 3.0) * U0.b + (1.0 / 3.0) * (U.b - h * R[1]);
                     U.c = (2.0 / 3.0) * U0.c + (1.0 / 3.0) * (U.c - h * R[2]);
@@ -333,18 +341,22 @@ __global__ void __launch_bounds__(BLOCK) k_flux(const DevGeom g, const Physics p
                     U.b = ms * tx;
                     U.c = ms * ty;
                 }
-                st.U[d] = U;
+                st.U[t] = U;
             }
             V4 qn;
             double rho, u, v, p;
             cons_to_q(U, ph, qn, rho, u, v, p);
-            q_out[d] = qn;
+            q_out[t] = qn;
             if (!physical(rho, u, v, p)) atomicOr(st.status, 1);
         }
     }
     if (MODE == 1) {
-        const double s = block_sum<BLOCK>(r2);
-        if (threadIdx.x == 0) st.partials[blockIdx.x] = s;
+        if (g.cshift == 0) {  // one condition: fused block partial sums
+            const double s = block_sum<BLOCK>(r2);
+            if (threadIdx.x == 0) st.partials[blockIdx.x] = s;
+        } else if (d < g.n) {  // several: per (point, condition), reduced per condition
+            st.r2[t] = r2;
+        }
     }
 }
 
@@ -366,63 +378,127 @@ __global__ void __launch_bounds__(kReduceBlock) k_residue(const DevState st, int
 
 // ------------------------------------------------------------ state I/O
 
-__global__ void k_set_uniform(const DevGeom g, const Physics ph, const V4 W, V4* U, V4* q) {
-    const int64_t d = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+__global__ void k_set_uniform(const DevGeom g, const Physics ph, const V4* __restrict__ Wc,
+                              V4* U, V4* q) {
+    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t d = t >> g.cshift;
     if (d >= g.n) return;
+    const V4 W = Wc[uint32_t(t) & g.cmask];
     V4 u;
     u.a = W.a;
     u.b = W.a * W.b;
     u.c = W.a * W.c;
     u.d = W.d * ph.gm1_inv + 0.5 * W.a * (W.b * W.b + W.c * W.c);
-    U[d] = u;
+    U[t] = u;
     V4 qq;
     double rho, uu, vv, p;
     cons_to_q(u, ph, qq, rho, uu, vv, p);
-    q[d] = qq;
+    q[t] = qq;
 }
 
+// W_user is condition-major in the caller's point order: [condition][point].
 __global__ void k_set_prim(const DevGeom g, const Physics ph, const V4* __restrict__ W_user,
                            V4* U, V4* q, int* status) {
-    const int64_t d = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t d = t >> g.cshift;
     if (d >= g.n) return;
-    const V4 W = W_user[g.dev_to_user[d]];
+    const int64_t cc = int64_t(uint32_t(t) & g.cmask);
+    const V4 W = W_user[cc * g.n + g.dev_to_user[d]];
     if (!physical(W.a, W.b, W.c, W.d)) atomicOr(status, 2);
     V4 u;
     u.a = W.a;
     u.b = W.a * W.b;
     u.c = W.a * W.c;
     u.d = W.d * ph.gm1_inv + 0.5 * W.a * (W.b * W.b + W.c * W.c);
-    U[d] = u;
+    U[t] = u;
     V4 qq;
     double rho, uu, vv, p;
     cons_to_q(u, ph, qq, rho, uu, vv, p);
-    q[d] = qq;
+    q[t] = qq;
 }
 
 __global__ void k_get_prim(const DevGeom g, const Physics ph, const V4* __restrict__ U,
                            V4* __restrict__ W_user) {
-    const int64_t d = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t d = t >> g.cshift;
     if (d >= g.n) return;
-    const V4 u = U[d];
+    const int64_t cc = int64_t(uint32_t(t) & g.cmask);
+    const V4 u = U[t];
     const double rho = u.a, uu = u.b / rho, vv = u.c / rho;
     const double p = ph.gm1 * (u.d - 0.5 * rho * (uu * uu + vv * vv));
-    W_user[g.dev_to_user[d]] = V4{rho, uu, vv, p};
+    W_user[cc * g.n + g.dev_to_user[d]] = V4{rho, uu, vv, p};
+}
+
+__global__ void k_q_from_U(const DevGeom g, const Physics ph, const V4* __restrict__ U,
+                           V4* __restrict__ q) {
+    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if ((t >> g.cshift) >= g.n) return;
+    V4 qq;
+    double rho, uu, vv, p;
+    cons_to_q(U[t], ph, qq, rho, uu, vv, p);
+    q[t] = qq;
 }
 
 template <typename T>
 __global__ void k_gather(const DevGeom g, const T* __restrict__ src, T* __restrict__ dst) {
-    const int64_t d = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t d = t >> g.cshift;
     if (d >= g.n) return;
-    dst[g.dev_to_user[d]] = src[d];
+    const int64_t cc = int64_t(uint32_t(t) & g.cmask);
+    dst[cc * g.n + g.dev_to_user[d]] = src[t];
 }
 
-// Pressure force on the wall loops: F = -sum (p_i - p_inf) n_i ds_i.
+// Residue per condition (C > 1), phase 1: block b reduces a contiguous range
+// of points for every condition into cpartials[b][c] (rows in a fixed order).
+__global__ void __launch_bounds__(512) k_residue_cond_p1(const DevGeom g, const DevState st) {
+    __shared__ double part[16][33];
+    const int64_t C = int64_t(1) << g.cshift;
+    const int64_t rows_per_block = (g.n + gridDim.x - 1) / gridDim.x;
+    const int64_t r0 = int64_t(blockIdx.x) * rows_per_block;
+    const int64_t r1 = min(g.n, r0 + rows_per_block);
+    for (int64_t c0 = 0; c0 < C; c0 += 32) {
+        const int64_t c = c0 + threadIdx.x;
+        double s = 0.0;
+        if (c < C)
+            for (int64_t r = r0 + threadIdx.y; r < r1; r += 16) s += st.r2[(r << g.cshift) | c];
+        part[threadIdx.y][threadIdx.x] = s;
+        __syncthreads();
+        if (threadIdx.y == 0 && c < C) {
+            double tot = 0.0;
+            for (int k = 0; k < 16; ++k) tot += part[k][threadIdx.x];
+            st.cpartials[int64_t(blockIdx.x) * C + c] = tot;
+        }
+        __syncthreads();
+    }
+}
+
+// Phase 2 (one block): sum the block partials of each condition in block
+// order, append sqrt(sum)/N per condition to the history.
+__global__ void __launch_bounds__(256) k_residue_cond_p2(const DevGeom g, const DevState st,
+                                                         int nblocks) {
+    const int64_t C = int64_t(1) << g.cshift;
+    const unsigned long long it = *st.iter_counter;
+    const int64_t slot = int64_t(it % (unsigned long long)(st.res_cap / C));
+    for (int64_t c = threadIdx.x; c < C; c += blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < nblocks; ++b) s += st.cpartials[int64_t(b) * C + c];
+        const double r = sqrt(s) / double(g.n);
+        st.res_hist[slot * C + c] = r;
+        if (!isfinite(r)) atomicOr(st.status, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *st.iter_counter = it + 1;
+}
+
+// Pressure force on the wall loops: F = -sum (p_i - p_inf) n_i ds_i; one
+// block per condition.
 __global__ void __launch_bounds__(kReduceBlock) k_forces(const DevGeom g, const Physics ph,
                                                          const DevState st) {
+    const uint32_t cc = blockIdx.x;
     double fx = 0.0, fy = 0.0;
     for (int64_t k = threadIdx.x; k < g.n_wall; k += kReduceBlock) {
         const int32_t d = g.wall_id[k];
-        const V4 u = st.U[d];
+        const V4 u = st.U[sidx(g, d, cc)];
         const double rho = u.a, uu = u.b / rho, vv = u.c / rho;
         const double p = ph.gm1 * (u.d - 0.5 * rho * (uu * uu + vv * vv));
         const double2 nds = g.wall_nds[k];
@@ -433,36 +509,38 @@ __global__ void __launch_bounds__(kReduceBlock) k_forces(const DevGeom g, const 
     __syncthreads();
     fy = block_sum<kReduceBlock>(fy);
     if (threadIdx.x == 0) {
-        st.force_out[0] = fx;
-        st.force_out[1] = fy;
+        st.force_out[2 * cc] = fx;
+        st.force_out[2 * cc + 1] = fy;
     }
 }
 
 inline unsigned grid_for(int64_t n, int block) { return unsigned((n + block - 1) / block); }
+// threads over all (point, condition) pairs
+inline unsigned grid_nc(const DevGeom& g, int block) { return grid_for(g.n << g.cshift, block); }
 
 }  // namespace
 
 cudaError_t launch_ls_first(const DevGeom& g, const V4* q, V8* dq, int block, cudaStream_t s) {
     if (block == 256)
-        k_ls_first<256><<<grid_for(g.n, 256), 256, 0, s>>>(g, q, dq);
+        k_ls_first<256><<<grid_nc(g, 256), 256, 0, s>>>(g, q, dq);
     else
-        k_ls_first<kDefaultBlock><<<grid_for(g.n, kDefaultBlock), kDefaultBlock, 0, s>>>(g, q, dq);
+        k_ls_first<kDefaultBlock><<<grid_nc(g, kDefaultBlock), kDefaultBlock, 0, s>>>(g, q, dq);
     return cudaGetLastError();
 }
 
 cudaError_t launch_ls_inner(const DevGeom& g, const V4* q, const V8* din, V8* dout, int block,
                             cudaStream_t s) {
     if (block == 256)
-        k_ls_inner<256><<<grid_for(g.n, 256), 256, 0, s>>>(g, q, din, dout);
+        k_ls_inner<256><<<grid_nc(g, 256), 256, 0, s>>>(g, q, din, dout);
     else
-        k_ls_inner<kDefaultBlock><<<grid_for(g.n, kDefaultBlock), kDefaultBlock, 0, s>>>(g, q, din, dout);
+        k_ls_inner<kDefaultBlock><<<grid_nc(g, kDefaultBlock), kDefaultBlock, 0, s>>>(g, q, din, dout);
     return cudaGetLastError();
 }
 
 template <int BLOCK, bool G14>
 static void flux_dispatch(int mode, const DevGeom& g, const Physics& ph, const DevState& st,
                           const V4* q_in, const V8* dq, V4* q_out, cudaStream_t s) {
-    const unsigned grid = grid_for(g.n, BLOCK);
+    const unsigned grid = grid_nc(g, BLOCK);
     switch (mode) {
         case 0: k_flux<0, BLOCK, G14><<<grid, BLOCK, 0, s>>>(g, ph, st, q_in, dq, q_out); break;
         case 1: k_flux<1, BLOCK, G14><<<grid, BLOCK, 0, s>>>(g, ph, st, q_in, dq, q_out); break;
@@ -491,36 +569,47 @@ cudaError_t launch_residue(const DevState& st, int nblocks, int64_t n, cudaStrea
     return cudaGetLastError();
 }
 
-cudaError_t launch_set_uniform(const DevGeom& g, const Physics& ph, V4 W, V4* U, V4* q,
+cudaError_t launch_residue_cond(const DevGeom& g, const DevState& st, cudaStream_t s) {
+    k_residue_cond_p1<<<kCondReduceBlocks, dim3(32, 16), 0, s>>>(g, st);
+    k_residue_cond_p2<<<1, 256, 0, s>>>(g, st, kCondReduceBlocks);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_uniform(const DevGeom& g, const Physics& ph, const V4* W_cond, V4* U, V4* q,
                                cudaStream_t s) {
-    k_set_uniform<<<grid_for(g.n, 256), 256, 0, s>>>(g, ph, W, U, q);
+    k_set_uniform<<<grid_nc(g, 256), 256, 0, s>>>(g, ph, W_cond, U, q);
     return cudaGetLastError();
 }
 
 cudaError_t launch_set_prim(const DevGeom& g, const Physics& ph, const V4* W_user, V4* U, V4* q,
                             int* status, cudaStream_t s) {
-    k_set_prim<<<grid_for(g.n, 256), 256, 0, s>>>(g, ph, W_user, U, q, status);
+    k_set_prim<<<grid_nc(g, 256), 256, 0, s>>>(g, ph, W_user, U, q, status);
     return cudaGetLastError();
 }
 
 cudaError_t launch_get_prim(const DevGeom& g, const Physics& ph, const V4* U, V4* W_user,
                             cudaStream_t s) {
-    k_get_prim<<<grid_for(g.n, 256), 256, 0, s>>>(g, ph, U, W_user);
+    k_get_prim<<<grid_nc(g, 256), 256, 0, s>>>(g, ph, U, W_user);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_q_from_U(const DevGeom& g, const Physics& ph, const V4* U, V4* q, cudaStream_t s) {
+    k_q_from_U<<<grid_nc(g, 256), 256, 0, s>>>(g, ph, U, q);
     return cudaGetLastError();
 }
 
 cudaError_t launch_gather_v4(const DevGeom& g, const V4* src, V4* dst, cudaStream_t s) {
-    k_gather<V4><<<grid_for(g.n, 256), 256, 0, s>>>(g, src, dst);
+    k_gather<V4><<<grid_nc(g, 256), 256, 0, s>>>(g, src, dst);
     return cudaGetLastError();
 }
 
 cudaError_t launch_gather_v8(const DevGeom& g, const V8* src, V8* dst, cudaStream_t s) {
-    k_gather<V8><<<grid_for(g.n, 256), 256, 0, s>>>(g, src, dst);
+    k_gather<V8><<<grid_nc(g, 256), 256, 0, s>>>(g, src, dst);
     return cudaGetLastError();
 }
 
 cudaError_t launch_forces(const DevGeom& g, const Physics& ph, const DevState& st, cudaStream_t s) {
-    k_forces<<<1, kReduceBlock, 0, s>>>(g, ph, st);
+    k_forces<<<unsigned(1u << g.cshift), kReduceBlock, 0, s>>>(g, ph, st);
     return cudaGetLastError();
 }
 

@@ -46,6 +46,13 @@ struct DevGeom {
     int64_t n;
     int64_t stride;  // row length of the slot-major arrays
     int slots;
+    // Conditions (free streams) solved together: C = 2^cshift, condition
+    // innermost. State index t = (point << cshift) | condition; thread t
+    // handles one (point, condition) pair, so the 32 lanes of a warp share one
+    // point's connectivity and weights (one broadcast load) and gather the
+    // neighbours' states of 32 consecutive conditions (one contiguous read).
+    int cshift;
+    uint32_t cmask;
     const int32_t* cnt;
     const int8_t* flag;
     const double2* nrm;
@@ -85,6 +92,8 @@ struct DevState {
     D8f* dq32[2]; // mixed precision: q-derivatives in FP32
     V4* R;     // residual output of the evaluation mode
     double* partials;  // per-block partial sums (scratch)
+    double* r2;        // C > 1: stage-1 R_rho^2 per (point, condition) (scratch)
+    double* cpartials; // C > 1: per-(block, condition) partial sums (scratch)
     double* res_hist;  // residue per iteration (ring buffer)
     int64_t res_cap;
     unsigned long long* iter_counter;
@@ -94,8 +103,14 @@ struct DevState {
 
 constexpr int kDefaultBlock = 128;
 constexpr int kReduceBlock = 512;
+constexpr int kCondReduceBlocks = 304;  // phase-1 blocks of the per-condition residue
 
 enum KernelClass { kFlux = 0, kLsFirst = 1, kLsInner = 2, kReduce = 3, kNumKernelClasses = 4 };
+
+// State index of (point d, condition c).
+__host__ __device__ __forceinline__ int64_t sidx(const DevGeom& g, int64_t d, uint32_t c) {
+    return (d << g.cshift) | int64_t(c);
+}
 
 // Launchers (return cudaGetLastError()).
 cudaError_t launch_ls_first(const DevGeom& g, const V4* q, V8* dq, int block, cudaStream_t s);
@@ -105,12 +120,16 @@ cudaError_t launch_ls_inner(const DevGeom& g, const V4* q, const V8* dq_in, V8* 
 cudaError_t launch_flux(int mode, const DevGeom& g, const Physics& ph, const DevState& st,
                         const V4* q_in, const V8* dq, V4* q_out, int block, cudaStream_t s);
 cudaError_t launch_residue(const DevState& st, int nblocks, int64_t n, cudaStream_t s);
-cudaError_t launch_set_uniform(const DevGeom& g, const Physics& ph, V4 W, V4* U, V4* q,
+// C > 1: residue per condition from st.r2 (two deterministic phases).
+cudaError_t launch_residue_cond(const DevGeom& g, const DevState& st, cudaStream_t s);
+// W_cond: device array of C primitive free-stream states.
+cudaError_t launch_set_uniform(const DevGeom& g, const Physics& ph, const V4* W_cond, V4* U, V4* q,
                                cudaStream_t s);
 cudaError_t launch_set_prim(const DevGeom& g, const Physics& ph, const V4* W_user, V4* U, V4* q,
                             int* status, cudaStream_t s);
 cudaError_t launch_get_prim(const DevGeom& g, const Physics& ph, const V4* U, V4* W_user,
                             cudaStream_t s);
+cudaError_t launch_q_from_U(const DevGeom& g, const Physics& ph, const V4* U, V4* q, cudaStream_t s);
 cudaError_t launch_gather_v4(const DevGeom& g, const V4* src_dev, V4* dst_user, cudaStream_t s);
 cudaError_t launch_gather_v8(const DevGeom& g, const V8* src_dev, V8* dst_user, cudaStream_t s);
 cudaError_t launch_forces(const DevGeom& g, const Physics& ph, const DevState& st,

@@ -45,20 +45,23 @@ template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK) k_ls_first_mx(const DevGeom g, const DevGeom32 g32,
                                                        const QHL* __restrict__ q,
                                                        D8f* __restrict__ dq) {
-    const int64_t d = int64_t(blockIdx.x) * BLOCK + threadIdx.x;
+    const int64_t t = int64_t(blockIdx.x) * BLOCK + threadIdx.x;  // (point, condition)
+    const int64_t d = t >> g.cshift;
+    const uint32_t cc = uint32_t(t) & g.cmask;
     if (d >= g.n) return;
-    const QHL qi = q[d];
+    const QHL qi = q[t];
     float4 ax = make_float4(0.f, 0.f, 0.f, 0.f), ay = ax;
     const int c = g.cnt[d];
+#pragma unroll 4
     for (int k = 0; k < c; ++k) {
         const int64_t at = int64_t(k) * g.stride + d;
         const uint32_t j = g.nbr[at] & kIndexMask;
         const float wx = g32.wx[at], wy = g32.wy[at];
-        const float4 dqv = qdiff(q[j], qi);
+        const float4 dqv = qdiff(q[sidx(g, j, cc)], qi);
         ax.x += wx * dqv.x; ax.y += wx * dqv.y; ax.z += wx * dqv.z; ax.w += wx * dqv.w;
         ay.x += wy * dqv.x; ay.y += wy * dqv.y; ay.z += wy * dqv.z; ay.w += wy * dqv.w;
     }
-    dq[d] = D8f{ax, ay};
+    dq[t] = D8f{ax, ay};
 }
 
 template <int BLOCK>
@@ -66,10 +69,12 @@ __global__ void __launch_bounds__(BLOCK) k_ls_inner_mx(const DevGeom g, const De
                                                        const QHL* __restrict__ q,
                                                        const D8f* __restrict__ din,
                                                        D8f* __restrict__ dout) {
-    const int64_t d = int64_t(blockIdx.x) * BLOCK + threadIdx.x;
+    const int64_t t = int64_t(blockIdx.x) * BLOCK + threadIdx.x;  // (point, condition)
+    const int64_t d = t >> g.cshift;
+    const uint32_t cc = uint32_t(t) & g.cmask;
     if (d >= g.n) return;
-    const QHL qi = q[d];
-    const D8f di = din[d];
+    const QHL qi = q[t];
+    const D8f di = din[t];
     float4 ax = make_float4(0.f, 0.f, 0.f, 0.f), ay = ax;
     const int c = g.cnt[d];
     for (int k = 0; k < c; ++k) {
@@ -77,8 +82,9 @@ __global__ void __launch_bounds__(BLOCK) k_ls_inner_mx(const DevGeom g, const De
         const uint32_t j = g.nbr[at] & kIndexMask;
         const float wx = g32.wx[at], wy = g32.wy[at];
         const float hx = g32.hdx[at], hy = g32.hdy[at];
-        const float4 dqv = qdiff(q[j], qi);
-        const D8f dj = din[j];
+        const int64_t jt = sidx(g, j, cc);
+        const float4 dqv = qdiff(q[jt], qi);
+        const D8f dj = din[jt];
         // dq~ = (q_j - q_i) - (dx (qx_j - qx_i) + dy (qy_j - qy_i)) / 2   (Eq. 28)
         const float t0 = dqv.x - (hx * (dj.x.x - di.x.x) + hy * (dj.y.x - di.y.x));
         const float t1 = dqv.y - (hx * (dj.x.y - di.x.y) + hy * (dj.y.y - di.y.y));
@@ -87,7 +93,7 @@ __global__ void __launch_bounds__(BLOCK) k_ls_inner_mx(const DevGeom g, const De
         ax.x += wx * t0; ax.y += wx * t1; ax.z += wx * t2; ax.w += wx * t3;
         ay.x += wy * t0; ay.y += wy * t1; ay.z += wy * t2; ay.w += wy * t3;
     }
-    dout[d] = D8f{ax, ay};
+    dout[t] = D8f{ax, ay};
 }
 
 // ------------------------------------------------ primitive base + difference
@@ -211,17 +217,30 @@ __device__ __forceinline__ void dsplit_flux_a(const float r0, const float ua0, c
     dG[3] = dQ * Aj + Q0 * dA + sg * (dRr * Bj + Rr0 * dB);
 }
 
+// q-variables (Eq. 26) from the conserved state, FP64 (the float-pair split
+// below needs q to ~1e-14). With beta = rho/(2p): q2 = 2 beta u1 = m1/p,
+// q3 = m2/p, q4 = -rho/p, beta |u|^2 = (|m|^2 / (2 rho)) / p, and for
+// gamma = 1.4 ln rho + ln(beta)/(gamma-1) = ln(rho beta^2 sqrt(beta)): one
+// logarithm and two reciprocals.
+template <bool G14>
 __device__ __forceinline__ void cons_to_q64(const V4& U, const Physics& ph, V4& q, double& rho,
                                             double& u, double& v, double& p) {
     rho = U.a;
-    u = U.b / rho;
-    v = U.c / rho;
-    p = ph.gm1 * (U.d - 0.5 * rho * (u * u + v * v));
-    const double beta = rho / (2.0 * p);
-    q.a = log(rho) + log(beta) * ph.gm1_inv - beta * (u * u + v * v);
-    q.b = 2.0 * beta * u;
-    q.c = 2.0 * beta * v;
-    q.d = -2.0 * beta;
+    const double irho = 1.0 / rho;
+    u = U.b * irho;
+    v = U.c * irho;
+    const double ke = 0.5 * (U.b * u + U.c * v);  // rho |u|^2 / 2
+    p = ph.gm1 * (U.d - ke);
+    const double ip = 1.0 / p;
+    const double beta = 0.5 * rho * ip;
+    if (G14) {
+        q.a = log(rho * (beta * beta) * sqrt(beta)) - ke * ip;
+    } else {
+        q.a = log(rho) + log(beta) * ph.gm1_inv - ke * ip;
+    }
+    q.b = U.b * ip;
+    q.c = U.c * ip;
+    q.d = -rho * ip;
 }
 
 __device__ __forceinline__ QHL split_hl(const V4& q) {
@@ -262,7 +281,9 @@ __global__ void __launch_bounds__(BLOCK) k_flux_mx(const DevGeom g, const DevGeo
                                                    const QHL* __restrict__ q_in,
                                                    const D8f* __restrict__ dq,
                                                    QHL* __restrict__ q_out) {
-    const int64_t d = int64_t(blockIdx.x) * BLOCK + threadIdx.x;
+    const int64_t t = int64_t(blockIdx.x) * BLOCK + threadIdx.x;  // (point, condition)
+    const int64_t d = t >> g.cshift;
+    const uint32_t cc = uint32_t(t) & g.cmask;
     double r2 = 0.0;
     if (d < g.n) {
         const int8_t fl = g.flag[d];
@@ -278,8 +299,8 @@ __global__ void __launch_bounds__(BLOCK) k_flux_mx(const DevGeom g, const DevGeo
                 tx = ny;
                 ty = -nx;
             }
-            const QHL qi = q_in[d];
-            const D8f di = dq[d];
+            const QHL qi = q_in[t];
+            const D8f di = dq[t];
             const float4 qiv = make_float4(qi.hi.x + qi.lo.x, qi.hi.y + qi.lo.y, qi.hi.z + qi.lo.z,
                                            qi.hi.w + qi.lo.w);
             const float gm1_inv = float(ph.gm1_inv);
@@ -291,11 +312,12 @@ __global__ void __launch_bounds__(BLOCK) k_flux_mx(const DevGeom g, const DevGeo
                 const uint32_t j = e & kIndexMask;
                 const uint32_t sc = (e >> kIndexBits) & 3u;
                 const uint32_t nc = (e >> (kIndexBits + 2)) & 3u;
-                const float4 dqv = qdiff(q_in[j], qi);
+                const int64_t jt = sidx(g, j, cc);
+                const float4 dqv = qdiff(q_in[jt], qi);
                 float4 base = qiv, dlt = dqv;
                 if (second) {
                     const float hx = g32.hdx[at], hy = g32.hdy[at];
-                    const D8f dj = dq[j];
+                    const D8f dj = dq[jt];
                     // q~_0 = q_i - (dx q_x,i + dy q_y,i)/2; dq~ = q~_j - q~_0 (Eq. 28)
                     base.x = qiv.x - (hx * di.x.x + hy * di.y.x);
                     base.y = qiv.y - (hx * di.x.y + hy * di.y.y);
@@ -339,24 +361,24 @@ __global__ void __launch_bounds__(BLOCK) k_flux_mx(const DevGeom g, const DevGeo
         // FP64 from here: state accumulation, wall condition, next q, residue
         const double R0 = R[0], R1 = R[1], R2 = R[2], R3 = R[3];
         if (MODE == 0) {
-            st.R[d] = V4{R0, R1, R2, R3};
+            st.R[t] = V4{R0, R1, R2, R3};
         } else {
-            V4 U = st.U[d];
+            V4 U = st.U[t];
             double dtv;
             if (MODE == 1) {
                 const double rho = U.a, u = U.b / rho, v = U.c / rho;
                 const double p = ph.gm1 * (U.d - 0.5 * rho * (u * u + v * v));
                 dtv = ph.cfl * g.dmin[d] / (sqrt(u * u + v * v) + sqrt(ph.gamma * p / rho));
-                st.dt[d] = dtv;
-                st.U0[d] = U;
+                st.dt[t] = dtv;
+                st.U0[t] = U;
                 r2 = R0 * R0;
             } else {
-                dtv = st.dt[d];
+                dtv = st.dt[t];
             }
             if (!fixed) {
                 const double h = 0.5 * dtv;
                 if (MODE == 3) {
-                    const V4 U0 = st.U0[d];
+                    const V4 U0 = st.U0[t];
                     U.a = (2.0 / 3.0) * U0.a + (1.0 / 3.0) * (U.a - h * R0);
                     U.b = (2.0 / 3.0) * U0.b + (1.0 / 3.0) * (U.b - h * R1);
                     U.c = (2.0 / 3.0) * U0.c + (1.0 / 3.0) * (U.c - h * R2);
@@ -374,48 +396,58 @@ __global__ void __launch_bounds__(BLOCK) k_flux_mx(const DevGeom g, const DevGeo
                     U.b = ms * tx;
                     U.c = ms * ty;
                 }
-                st.U[d] = U;
+                st.U[t] = U;
             }
             V4 qn;
             double rho, u, v, p;
-            cons_to_q64(U, ph, qn, rho, u, v, p);
-            q_out[d] = split_hl(qn);
+            cons_to_q64<G14>(U, ph, qn, rho, u, v, p);
+            q_out[t] = split_hl(qn);
             if (!physical(rho, u, v, p)) atomicOr(st.status, 1);
         }
     }
     if (MODE == 1) {
-        const double s = block_sum<BLOCK>(r2);
-        if (threadIdx.x == 0) st.partials[blockIdx.x] = s;
+        if (g.cshift == 0) {
+            const double s = block_sum<BLOCK>(r2);
+            if (threadIdx.x == 0) st.partials[blockIdx.x] = s;
+        } else if (d < g.n) {
+            st.r2[t] = r2;
+        }
     }
 }
 
 __global__ void k_q_from_U_mx(const DevGeom g, const Physics ph, const V4* __restrict__ U,
                               QHL* __restrict__ q) {
-    const int64_t d = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (d >= g.n) return;
+    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if ((t >> g.cshift) >= g.n) return;
     V4 qn;
     double rho, u, v, p;
-    cons_to_q64(U[d], ph, qn, rho, u, v, p);
-    q[d] = split_hl(qn);
+    if (fabs(ph.gm1_inv - 2.5) < 1e-12)
+        cons_to_q64<true>(U[t], ph, qn, rho, u, v, p);
+    else
+        cons_to_q64<false>(U[t], ph, qn, rho, u, v, p);
+    q[t] = split_hl(qn);
 }
 
 __global__ void k_dq_to_v8(const DevGeom g, const D8f* __restrict__ src, V8* __restrict__ dst) {
-    const int64_t d = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t d = t >> g.cshift;
     if (d >= g.n) return;
-    const D8f s = src[d];
+    const int64_t cc = int64_t(uint32_t(t) & g.cmask);
+    const D8f s = src[t];
     V8 o;
     o.x[0] = s.x.x; o.x[1] = s.x.y; o.x[2] = s.x.z; o.x[3] = s.x.w;
     o.y[0] = s.y.x; o.y[1] = s.y.y; o.y[2] = s.y.z; o.y[3] = s.y.w;
-    dst[g.dev_to_user[d]] = o;
+    dst[cc * g.n + g.dev_to_user[d]] = o;
 }
 
 inline unsigned grid_for(int64_t n, int block) { return unsigned((n + block - 1) / block); }
+inline unsigned grid_nc(const DevGeom& g, int block) { return grid_for(g.n << g.cshift, block); }
 
 template <int BLOCK, bool G14>
 void flux_mx_dispatch(int mode, const DevGeom& g, const DevGeom32& g32, const Physics& ph,
                       const DevState& st, const QHL* q_in, const D8f* dq, QHL* q_out,
                       cudaStream_t s) {
-    const unsigned grid = grid_for(g.n, BLOCK);
+    const unsigned grid = grid_nc(g, BLOCK);
     switch (mode) {
         case 0: k_flux_mx<0, BLOCK, G14><<<grid, BLOCK, 0, s>>>(g, g32, ph, st, q_in, dq, q_out); break;
         case 1: k_flux_mx<1, BLOCK, G14><<<grid, BLOCK, 0, s>>>(g, g32, ph, st, q_in, dq, q_out); break;
@@ -430,18 +462,18 @@ void flux_mx_dispatch(int mode, const DevGeom& g, const DevGeom32& g32, const Ph
 cudaError_t launch_ls_first_mx(const DevGeom& g, const DevGeom32& g32, const QHL* q, D8f* dq,
                                int block, cudaStream_t s) {
     if (block == 256)
-        k_ls_first_mx<256><<<grid_for(g.n, 256), 256, 0, s>>>(g, g32, q, dq);
+        k_ls_first_mx<256><<<grid_nc(g, 256), 256, 0, s>>>(g, g32, q, dq);
     else
-        k_ls_first_mx<kDefaultBlock><<<grid_for(g.n, kDefaultBlock), kDefaultBlock, 0, s>>>(g, g32, q, dq);
+        k_ls_first_mx<kDefaultBlock><<<grid_nc(g, kDefaultBlock), kDefaultBlock, 0, s>>>(g, g32, q, dq);
     return cudaGetLastError();
 }
 
 cudaError_t launch_ls_inner_mx(const DevGeom& g, const DevGeom32& g32, const QHL* q,
                                const D8f* din, D8f* dout, int block, cudaStream_t s) {
     if (block == 256)
-        k_ls_inner_mx<256><<<grid_for(g.n, 256), 256, 0, s>>>(g, g32, q, din, dout);
+        k_ls_inner_mx<256><<<grid_nc(g, 256), 256, 0, s>>>(g, g32, q, din, dout);
     else
-        k_ls_inner_mx<kDefaultBlock><<<grid_for(g.n, kDefaultBlock), kDefaultBlock, 0, s>>>(g, g32, q, din, dout);
+        k_ls_inner_mx<kDefaultBlock><<<grid_nc(g, kDefaultBlock), kDefaultBlock, 0, s>>>(g, g32, q, din, dout);
     return cudaGetLastError();
 }
 
@@ -461,12 +493,12 @@ cudaError_t launch_flux_mx(int mode, const DevGeom& g, const DevGeom32& g32, con
 
 cudaError_t launch_q_from_U_mx(const DevGeom& g, const Physics& ph, const V4* U, QHL* q,
                                cudaStream_t s) {
-    k_q_from_U_mx<<<grid_for(g.n, 256), 256, 0, s>>>(g, ph, U, q);
+    k_q_from_U_mx<<<grid_nc(g, 256), 256, 0, s>>>(g, ph, U, q);
     return cudaGetLastError();
 }
 
 cudaError_t launch_dq_to_user_mx(const DevGeom& g, const D8f* src, V8* dst_user, cudaStream_t s) {
-    k_dq_to_v8<<<grid_for(g.n, 256), 256, 0, s>>>(g, src, dst_user);
+    k_dq_to_v8<<<grid_nc(g, 256), 256, 0, s>>>(g, src, dst_user);
     return cudaGetLastError();
 }
 

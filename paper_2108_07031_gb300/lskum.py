@@ -33,9 +33,9 @@ KERNEL_FLUX, KERNEL_LS_FIRST, KERNEL_LS_INNER, KERNEL_REDUCE = 0, 1, 2, 3
 # every exported entry point of include/lskum.h
 EXPORTED = (
     "lskum_default_options", "lskum_create", "lskum_destroy", "lskum_set_stream",
-    "lskum_set_freestream", "lskum_set_state", "lskum_get_state", "lskum_step", "lskum_solve",
+    "lskum_set_freestream", "lskum_set_conditions", "lskum_set_state", "lskum_get_state", "lskum_step", "lskum_solve",
     "lskum_residual_norm", "lskum_forces", "lskum_eval_residual", "lskum_eval_q_derivatives",
-    "lskum_info", "lskum_profile", "lskum_kernel_time", "lskum_last_launch_count",
+    "lskum_info", "lskum_autotune", "lskum_profile", "lskum_kernel_time", "lskum_last_launch_count",
     "lskum_error_string", "lskum_last_error", "lskum_residue_noalloc",
 )
 
@@ -52,7 +52,7 @@ class Options(C.Structure):
     _fields_ = [("gamma", C.c_double), ("cfl", C.c_double), ("inner_iters", C.c_int),
                 ("order", C.c_int), ("wall_factor", C.c_double), ("outer_mode", C.c_int),
                 ("precision", C.c_int), ("reorder", C.c_int), ("block_size", C.c_int),
-                ("check_every", C.c_int)]
+                ("check_every", C.c_int), ("n_conditions", C.c_int)]
 
 
 def library_path() -> str:
@@ -78,6 +78,7 @@ def load(build_if_missing: bool = True):
             "lskum_destroy": ([P], None),
             "lskum_set_stream": ([P, P], I),
             "lskum_set_freestream": ([P, D, D], I),
+            "lskum_set_conditions": ([P, I, P, P], I),
             "lskum_set_state": ([P, P], I),
             "lskum_get_state": ([P, P], I),
             "lskum_step": ([P, I], I),
@@ -86,7 +87,8 @@ def load(build_if_missing: bool = True):
             "lskum_forces": ([P, P, P], I),
             "lskum_eval_residual": ([P, P], I),
             "lskum_eval_q_derivatives": ([P, P, P], I),
-            "lskum_info": ([P, P, P, P], I),
+            "lskum_info": ([P, P, P, P, P], I),
+            "lskum_autotune": ([P, I, P], I),
             "lskum_profile": ([P, I], I),
             "lskum_kernel_time": ([P, I, P, P], I),
             "lskum_last_launch_count": ([P], I64),
@@ -157,6 +159,7 @@ class Solver:
             raise ValueError("nbr_offsets must have n + 1 entries")
         opt = options if options is not None else default_options(**overrides)
         self.options = opt
+        self.n_cond = int(opt.n_conditions)
         h = C.c_void_p()
         _check(lib.lskum_create(n, _ptr(xy), _ptr(nrm), _ptr(fl), _ptr(off), _ptr(idx),
                                 C.byref(opt), C.byref(h)), "lskum_create")
@@ -193,8 +196,19 @@ class Solver:
         _check(self._lib.lskum_set_freestream(self._h, float(mach), float(alpha_deg)),
                "lskum_set_freestream")
 
+    def set_conditions(self, mach, alpha_deg):
+        m = np.ascontiguousarray(mach, dtype=np.float64).reshape(-1)
+        a = np.ascontiguousarray(alpha_deg, dtype=np.float64).reshape(-1)
+        if m.size != a.size:
+            raise ValueError("mach and alpha_deg differ in length")
+        _check(self._lib.lskum_set_conditions(self._h, int(m.size), _ptr(m), _ptr(a)),
+               "lskum_set_conditions")
+
+    def _shape(self, m=4):
+        return (self.n, m) if self.n_cond == 1 else (self.n_cond, self.n, m)
+
     def set_state(self, prim):
-        W = _host_f64(prim, (self.n, 4))
+        W = _host_f64(prim, self._shape())
         _check(self._lib.lskum_set_state(self._h, _ptr(W)), "lskum_set_state")
 
     def set_state_ptr(self, host_ptr: int):
@@ -202,7 +216,7 @@ class Solver:
         _check(self._lib.lskum_set_state(self._h, C.c_void_p(host_ptr)), "lskum_set_state")
 
     def get_state(self) -> np.ndarray:
-        W = np.empty((self.n, 4), dtype=np.float64)
+        W = np.empty(self._shape(), dtype=np.float64)
         _check(self._lib.lskum_get_state(self._h, _ptr(W)), "lskum_get_state")
         return W
 
@@ -216,33 +230,47 @@ class Solver:
                "lskum_solve")
         return done.value
 
-    def residual_norm(self) -> float:
-        r = C.c_double()
-        _check(self._lib.lskum_residual_norm(self._h, C.byref(r)), "lskum_residual_norm")
-        return r.value
+    def residual_norm(self):
+        """Residue of the last iteration (a float, or an array per condition)."""
+        r = np.zeros(self.n_cond, dtype=np.float64)
+        _check(self._lib.lskum_residual_norm(self._h, _ptr(r)), "lskum_residual_norm")
+        return float(r[0]) if self.n_cond == 1 else r
 
     def forces(self):
-        cl, cd = C.c_double(), C.c_double()
-        _check(self._lib.lskum_forces(self._h, C.byref(cl), C.byref(cd)), "lskum_forces")
-        return cl.value, cd.value
+        """(Cl, Cd), as floats or as arrays per condition."""
+        cl = np.zeros(self.n_cond, dtype=np.float64)
+        cd = np.zeros(self.n_cond, dtype=np.float64)
+        _check(self._lib.lskum_forces(self._h, _ptr(cl), _ptr(cd)), "lskum_forces")
+        if self.n_cond == 1:
+            return float(cl[0]), float(cd[0])
+        return cl, cd
 
     # -- evaluation hooks (tests, diagnostics)
     def eval_residual(self) -> np.ndarray:
-        R = np.empty((self.n, 4), dtype=np.float64)
+        R = np.empty(self._shape(), dtype=np.float64)
         _check(self._lib.lskum_eval_residual(self._h, _ptr(R)), "lskum_eval_residual")
         return R
 
     def eval_q_derivatives(self):
-        qx = np.empty((self.n, 4), dtype=np.float64)
-        qy = np.empty((self.n, 4), dtype=np.float64)
+        qx = np.empty(self._shape(), dtype=np.float64)
+        qy = np.empty(self._shape(), dtype=np.float64)
         _check(self._lib.lskum_eval_q_derivatives(self._h, _ptr(qx), _ptr(qy)),
                "lskum_eval_q_derivatives")
         return qx, qy
 
     def info(self):
-        n, nw, mx = C.c_int64(), C.c_int64(), C.c_int()
-        _check(self._lib.lskum_info(self._h, C.byref(n), C.byref(nw), C.byref(mx)), "lskum_info")
-        return {"n_points": n.value, "n_wall": nw.value, "max_neighbours": mx.value}
+        n, nw, mx, nc = C.c_int64(), C.c_int64(), C.c_int(), C.c_int()
+        _check(self._lib.lskum_info(self._h, C.byref(n), C.byref(nw), C.byref(mx), C.byref(nc)),
+               "lskum_info")
+        return {"n_points": n.value, "n_wall": nw.value, "max_neighbours": mx.value,
+                "n_conditions": nc.value}
+
+    def autotune(self, trial_iters: int = 2):
+        """Pick the fastest (flux block, derivative block); returns the pair."""
+        best = C.c_int()
+        _check(self._lib.lskum_autotune(self._h, int(trial_iters), C.byref(best)),
+               "lskum_autotune")
+        return divmod(best.value, 1000)
 
     def profile(self, enable: bool):
         _check(self._lib.lskum_profile(self._h, 1 if enable else 0), "lskum_profile")
