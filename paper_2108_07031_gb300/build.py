@@ -20,7 +20,8 @@ LIB = os.path.join(BUILD, "liblskum.so")
 PROBE = os.path.join(BUILD, "pipe_peaks")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CUDA_SOURCES = ["lskum_kernels.cu", "lskum_kernels_mixed.cu", "lskum_api.cu", "lskum_noalloc.cu"]
+CUDA_SOURCES = ["lskum_kernels.cu", "lskum_kernels_mixed.cu", "lskum_api.cu", "lskum_noalloc.cu",
+                "mlp_kernels.cu"]
 HOST_SOURCES = ["lskum_setup.cpp"]
 HEADERS = ["lskum_internal.h", "lskum_kernels.cuh", "erfc_tables.h"]
 
@@ -44,7 +45,8 @@ def build(force: bool = False, verbose: bool = False, fmad: bool = True) -> str:
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
     inc = os.path.join(os.path.dirname(HERE), "include")
-    headers = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(inc, "lskum.h")]
+    headers = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(inc, "lskum.h"),
+                                                           os.path.join(inc, "lskum_mlp.h")]
     cuda_flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", inc,
                          "--fmad=true" if fmad else "--fmad=false"]
     jobs = []

@@ -1,0 +1,524 @@
+// Warm-start surrogate: a coordinate/condition MLP trained and evaluated on
+// the GPU with hand-written BF16 tensor-core kernels (FP32 accumulation).
+//
+// Network (include/lskum_mlp.h): 21 input features (zero-padded to 32) ->
+// 5 hidden layers of 256 (tanh) -> 4 outputs (linear): six linear layers.
+// Z_l = X_l W_l^T + b_l, X_{l+1} = tanh(Z_l). Weights are kept in FP32
+// (Adam master copy) and in BF16 (W) for the GEMMs;
+// activations are stored FP32 (for tanh') and BF16 (GEMM input).
+//
+// GEMM: C[M x N] = A[M x K] B[K x N], A and B BF16 in global memory with
+// arbitrary element strides (so the forward X W^T, the backward dZ W and
+// the weight gradient dZ^T X all use one kernel), staged through shared
+// memory as A[m][k] and B[n][k] (k contiguous), 64 x 64 tiles per block of
+// four warps, mma.sync m16n8k16 (bf16 x bf16 -> f32).
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/lskum_mlp.h"
+#include "lskum_internal.h"
+
+namespace mlpk {
+
+constexpr int kTile = 64;
+constexpr int kKt = 32;             // k per shared-memory stage
+constexpr int kSmemPad = 8;         // bf16 padding per row (bank spread)
+constexpr int kLayers = LSKUM_MLP_LAYERS;
+constexpr int kWidth = LSKUM_MLP_WIDTH;
+constexpr int kIn = LSKUM_MLP_IN_PADDED;
+constexpr int kOut = LSKUM_MLP_OUT;
+
+__host__ __device__ inline int layer_in(int l) { return l == 0 ? kIn : kWidth; }
+__host__ __device__ inline int layer_out(int l) { return l == kLayers - 1 ? kOut : kWidth; }
+
+__device__ __forceinline__ uint32_t ld_pair(const __nv_bfloat16* p) {
+    return *reinterpret_cast<const uint32_t*>(p);
+}
+
+__device__ __forceinline__ void mma_bf16_16816(float c[4], const uint32_t a[4], const uint32_t b[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+        "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+enum Epilogue { kStoreF32 = 0, kBiasTanh = 1, kBiasLinear = 2 };
+
+// C = A B with A(m, k) = A[m * sam + k * sak], B(k, n) = B[k * sbk + n * sbn].
+// Epilogue kBiasTanh: Zf = C + bias[n], Af = tanh(Zf), Ab = bf16(Af);
+// kBiasLinear: Cf = C + bias[n]; kStoreF32: Cf = C. Row-major outputs with
+// leading dimension ldc.
+template <int EPI>
+__global__ void __launch_bounds__(128) k_gemm_bf16(const __nv_bfloat16* __restrict__ A, int64_t sam,
+                                                   int64_t sak, const __nv_bfloat16* __restrict__ B,
+                                                   int64_t sbk, int64_t sbn, int M, int N, int K,
+                                                   const float* __restrict__ bias,
+                                                   float* __restrict__ Cf,
+                                                   __nv_bfloat16* __restrict__ Cb, int64_t ldc) {
+    __shared__ __align__(16) __nv_bfloat16 As[kTile][kKt + kSmemPad];
+    __shared__ __align__(16) __nv_bfloat16 Bs[kTile][kKt + kSmemPad];
+    const int m0 = blockIdx.y * kTile, n0 = blockIdx.x * kTile;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;  // warp tile origin
+    const int grp = lane >> 2, tig = lane & 3;
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
+    const __nv_bfloat16 zero = __float2bfloat16(0.f);
+    const bool a_kfast = sak == 1, b_kfast = sbk == 1;
+    for (int k0 = 0; k0 < K; k0 += kKt) {
+        // stage: 64 x 32 elements of each operand, 16 per thread; consecutive
+        // threads walk the operand's contiguous dimension (coalesced loads)
+        for (int e = tid; e < kTile * kKt; e += 128) {
+            const int r = a_kfast ? e / kKt : e % kTile;
+            const int kk = a_kfast ? e % kKt : e / kTile;
+            const int gm = m0 + r, gk = k0 + kk;
+            As[r][kk] = (gm < M && gk < K) ? A[gm * sam + gk * sak] : zero;
+        }
+        for (int e = tid; e < kTile * kKt; e += 128) {
+            const int r = b_kfast ? e / kKt : e % kTile;
+            const int kk = b_kfast ? e % kKt : e / kTile;
+            const int gn = n0 + r, gk = k0 + kk;
+            Bs[r][kk] = (gn < N && gk < K) ? B[gk * sbk + gn * sbn] : zero;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int ks = 0; ks < kKt; ks += 16) {
+            uint32_t af[2][4], bfr[4][2];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int row = wm + i * 16 + grp;
+                const int col = ks + tig * 2;
+                af[i][0] = ld_pair(&As[row][col]);
+                af[i][1] = ld_pair(&As[row + 8][col]);
+                af[i][2] = ld_pair(&As[row][col + 8]);
+                af[i][3] = ld_pair(&As[row + 8][col + 8]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int n = wn + j * 8 + grp;
+                const int k = ks + tig * 2;
+                bfr[j][0] = ld_pair(&Bs[n][k]);
+                bfr[j][1] = ld_pair(&Bs[n][k + 8]);
+            }
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) mma_bf16_16816(acc[i][j], af[i], bfr[j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int m = m0 + wm + i * 16 + grp + ((r & 2) ? 8 : 0);
+                const int n = n0 + wn + j * 8 + tig * 2 + (r & 1);
+                if (m >= M || n >= N) continue;
+                float v = acc[i][j][r];
+                if (EPI != kStoreF32) v += bias[n];
+                if (EPI == kBiasTanh) {
+                    const float a = tanhf(v);
+                    Cf[int64_t(m) * ldc + n] = a;
+                    Cb[int64_t(m) * ldc + n] = __float2bfloat16(a);
+                } else {
+                    Cf[int64_t(m) * ldc + n] = v;
+                }
+            }
+}
+
+// Features: per sample raw (x, y, wall distance, M, alpha_deg) ->
+// [x/10, y/10, log(d + 1e-3)/5, (M - 0.55)/0.25, (alpha - 1)/5,
+//  sin(P (x, y)), cos(P (x, y)) (8 projections each), 0 x 11 padding],
+// stored FP32 (the caller-visible encoding) and BF16 (GEMM input).
+__global__ void k_features(const float* __restrict__ raw, int64_t n, const float* __restrict__ proj,
+                           float* __restrict__ feat) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float* r = raw + 5 * i;
+    float* f = feat + int64_t(kIn) * i;
+    const float x = r[0], y = r[1];
+    f[0] = x * 0.1f;
+    f[1] = y * 0.1f;
+    f[2] = logf(r[2] + 1e-3f) * 0.2f;
+    f[3] = (r[3] - 0.55f) * 4.0f;
+    f[4] = (r[4] - 1.0f) * 0.2f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const float t = proj[2 * k] * x + proj[2 * k + 1] * y;
+        f[5 + k] = sinf(t);
+        f[13 + k] = cosf(t);
+    }
+#pragma unroll
+    for (int k = 21; k < kIn; ++k) f[k] = 0.f;
+}
+
+__global__ void k_to_bf16(const float* __restrict__ src, int64_t n, __nv_bfloat16* __restrict__ dst) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = __float2bfloat16(src[i]);
+}
+
+// MSE loss pieces: dY = 2 (Y - T) / (n * 4), per-block partial sums of (Y-T)^2.
+__global__ void __launch_bounds__(256) k_mse(const float* __restrict__ Y, const float* __restrict__ T,
+                                             int64_t n, float* __restrict__ dY,
+                                             double* __restrict__ partial) {
+    const int64_t i = int64_t(blockIdx.x) * 256 + threadIdx.x;
+    double s = 0.0;
+    if (i < n * kOut) {
+        const float d = Y[i] - T[i];
+        dY[i] = 2.0f * d / float(n * kOut);
+        s = double(d) * d;
+    }
+    __shared__ double sh[256];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+}
+
+__global__ void k_sum_partials(const double* __restrict__ partial, int nb, int64_t count,
+                               double* __restrict__ out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += partial[b];
+    *out = s / double(count);
+}
+
+// dZ = dA * (1 - A^2) (tanh'), FP32 and BF16 copies.
+__global__ void k_tanh_back(const float* __restrict__ dA, const float* __restrict__ A, int64_t n,
+                            float* __restrict__ dZ, __nv_bfloat16* __restrict__ dZb) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float a = A[i];
+    const float v = dA[i] * (1.0f - a * a);
+    dZ[i] = v;
+    dZb[i] = __float2bfloat16(v);
+}
+
+// db[c] = sum over rows of dZ[r][c], rows summed in a fixed order.
+__global__ void __launch_bounds__(256) k_colsum(const float* __restrict__ dZ, int rows, int cols,
+                                                float* __restrict__ db) {
+    __shared__ float sh[8][33];
+    const int c = blockIdx.x * 32 + threadIdx.x;
+    float s = 0.f;
+    if (c < cols)
+        for (int r = threadIdx.y; r < rows; r += 8) s += dZ[int64_t(r) * cols + c];
+    sh[threadIdx.y][threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.y == 0 && c < cols) {
+        float t = 0.f;
+        for (int k = 0; k < 8; ++k) t += sh[k][threadIdx.x];
+        db[c] = t;
+    }
+}
+
+// Adam on the flat FP32 parameter vector; the BF16 copy W is refreshed after it.
+struct LayerPtrs {
+    int64_t w_off[kLayers];  // offsets of W_l and b_l in the flat vector
+    int64_t b_off[kLayers];
+    __nv_bfloat16* W[kLayers];
+};
+
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, int64_t n, float lr, float b1, float b2, float eps,
+                       float c1, float c2) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+}
+
+__global__ void k_weights_bf16(const float* __restrict__ p, LayerPtrs L) {
+    const int l = blockIdx.y;
+    const int K = layer_in(l), N = layer_out(l);
+    const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e >= int64_t(K) * N) return;
+    const int nrow = int(e / K), k = int(e % K);
+    float w = p[L.w_off[l] + e];
+    if (l == 0 && k >= 21) w = 0.f;  // padded inputs carry no weight
+    L.W[l][e] = __float2bfloat16(w);
+    (void)nrow;
+}
+
+}  // namespace mlpk
+
+// ------------------------------------------------------------------ C ABI
+
+using namespace mlpk;
+
+struct lskum_mlp {
+    cudaStream_t stream = nullptr;
+    int64_t cap = 0;  // samples per call
+    int64_t nparam = 0;
+    LayerPtrs L{};
+    float* p = nullptr;   // FP32 master parameters
+    float* g = nullptr;   // gradients
+    float* m = nullptr;   // Adam moments
+    float* v = nullptr;
+    float* proj = nullptr;  // 8 x 2 Fourier projection
+    int64_t step = 0;
+    // activations: Af[l] (FP32) and Ab[l] (BF16) for l = 0..kLayers (l = 0: features)
+    float* Af[kLayers + 1] = {nullptr};
+    __nv_bfloat16* Ab[kLayers + 1] = {nullptr};
+    float* dA = nullptr;   // cap x 256 scratch
+    float* dZ = nullptr;   // cap x 256
+    __nv_bfloat16* dZb = nullptr;
+    double* partial = nullptr;
+    double* loss_dev = nullptr;
+    std::vector<void*> allocs;
+};
+
+namespace {
+
+int fail(int code, const std::string& m) {
+    lskum::set_last_error(m);
+    return code;
+}
+
+#define MLP_CUDA(x)                                                                    \
+    do {                                                                               \
+        cudaError_t e_ = (x);                                                          \
+        if (e_ != cudaSuccess) return fail(LSKUM_ERR_CUDA, std::string(#x) + ": " +     \
+                                                           cudaGetErrorString(e_));    \
+    } while (0)
+
+template <typename T>
+cudaError_t alloc(lskum_mlp* h, T** p, int64_t count) {
+    void* raw = nullptr;
+    cudaError_t e = cudaMalloc(&raw, sizeof(T) * size_t(count > 0 ? count : 1));
+    if (e == cudaSuccess) h->allocs.push_back(raw);
+    *p = static_cast<T*>(raw);
+    return e;
+}
+
+inline unsigned blocks(int64_t n, int b) { return unsigned((n + b - 1) / b); }
+
+template <int EPI>
+cudaError_t gemm(lskum_mlp* h, const __nv_bfloat16* A, int64_t sam, int64_t sak,
+                 const __nv_bfloat16* B, int64_t sbk, int64_t sbn, int M, int N, int K,
+                 const float* bias, float* Cf, __nv_bfloat16* Cb, int64_t ldc) {
+    dim3 grid(blocks(N, kTile), blocks(M, kTile));
+    k_gemm_bf16<EPI><<<grid, 128, 0, h->stream>>>(A, sam, sak, B, sbk, sbn, M, N, K, bias, Cf, Cb, ldc);
+    return cudaGetLastError();
+}
+
+// forward from features (FP32 n x 32 in h->Af[0]); output Af[kLayers] (n x 4)
+int forward(lskum_mlp* h, int64_t n) {
+    MLP_CUDA((k_to_bf16<<<blocks(n * kIn, 256), 256, 0, h->stream>>>(h->Af[0], n * kIn, h->Ab[0]),
+              cudaGetLastError()));
+    for (int l = 0; l < kLayers; ++l) {
+        const int K = layer_in(l), N = layer_out(l);
+        const float* b = h->p + h->L.b_off[l];
+        cudaError_t e;
+        if (l < kLayers - 1)
+            e = gemm<kBiasTanh>(h, h->Ab[l], K, 1, h->L.W[l], 1, K, int(n), N, K, b, h->Af[l + 1],
+                                h->Ab[l + 1], N);
+        else
+            e = gemm<kBiasLinear>(h, h->Ab[l], K, 1, h->L.W[l], 1, K, int(n), N, K, b, h->Af[l + 1],
+                                  nullptr, N);
+        if (e != cudaSuccess) return fail(LSKUM_ERR_CUDA, std::string("forward: ") + cudaGetErrorString(e));
+    }
+    return LSKUM_OK;
+}
+
+// backward from targets T (device n x 4): gradients into h->g, loss into loss_dev
+int backward(lskum_mlp* h, const float* T, int64_t n) {
+    const int nb = int(blocks(n * kOut, 256));
+    MLP_CUDA((k_mse<<<nb, 256, 0, h->stream>>>(h->Af[kLayers], T, n, h->dZ, h->partial), cudaGetLastError()));
+    MLP_CUDA((k_sum_partials<<<1, 32, 0, h->stream>>>(h->partial, nb, n * kOut, h->loss_dev), cudaGetLastError()));
+    // output layer: dZ (n x 4) FP32 in h->dZ
+    MLP_CUDA((k_to_bf16<<<blocks(n * kOut, 256), 256, 0, h->stream>>>(h->dZ, n * kOut, h->dZb), cudaGetLastError()));
+    for (int l = kLayers - 1; l >= 0; --l) {
+        const int K = layer_in(l), N = layer_out(l);
+        // dW_l [N x K] = dZ^T X_l : A(m = out unit, k = sample) = dZ[s][m], B(k = sample, n = in) = X[s][n]
+        cudaError_t e = gemm<kStoreF32>(h, h->dZb, 1, N, h->Ab[l], K, 1, N, K, int(n), nullptr,
+                                        h->g + h->L.w_off[l], nullptr, K);
+        if (e != cudaSuccess) return fail(LSKUM_ERR_CUDA, std::string("dW: ") + cudaGetErrorString(e));
+        MLP_CUDA((k_colsum<<<blocks(N, 32), dim3(32, 8), 0, h->stream>>>(h->dZ, int(n), N, h->g + h->L.b_off[l]),
+                  cudaGetLastError()));
+        if (l == 0) break;
+        // dA_{l} [n x K] = dZ W_l : A(m = sample, k = out) = dZ, B(k = out, n = in) = W[out][in]
+        e = gemm<kStoreF32>(h, h->dZb, N, 1, h->L.W[l], K, 1, int(n), K, N, nullptr, h->dA, nullptr, K);
+        if (e != cudaSuccess) return fail(LSKUM_ERR_CUDA, std::string("dA: ") + cudaGetErrorString(e));
+        MLP_CUDA((k_tanh_back<<<blocks(n * K, 256), 256, 0, h->stream>>>(h->dA, h->Af[l], n * K, h->dZ, h->dZb),
+                  cudaGetLastError()));
+    }
+    return LSKUM_OK;
+}
+
+int check_n(lskum_mlp* h, int64_t n) {
+    if (n < 1 || n > h->cap)
+        return fail(LSKUM_ERR_INVALID_ARG, "n = " + std::to_string(n) + " outside [1, " +
+                                               std::to_string(h->cap) + "]");
+    return LSKUM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t lskum_mlp_num_params(void) {
+    int64_t s = 0;
+    for (int l = 0; l < kLayers; ++l) s += int64_t(layer_in(l)) * layer_out(l) + layer_out(l);
+    return s;
+}
+
+int lskum_mlp_create(int64_t capacity, const float* proj, lskum_mlp** out) {
+    if (!out || !proj || capacity < 1 || capacity > (int64_t(1) << 24))
+        return fail(LSKUM_ERR_INVALID_ARG, "lskum_mlp_create: invalid argument");
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0)
+        return fail(LSKUM_ERR_CUDA, "lskum_mlp_create: no usable CUDA device");
+    lskum_mlp* h = new lskum_mlp();
+    h->cap = capacity;
+    h->nparam = lskum_mlp_num_params();
+    auto bail = [&](cudaError_t e) {
+        for (void* p : h->allocs) cudaFree(p);
+        if (h->stream) cudaStreamDestroy(h->stream);
+        delete h;
+        return fail(LSKUM_ERR_CUDA, std::string("lskum_mlp_create: ") + cudaGetErrorString(e));
+    };
+    cudaError_t e;
+    if ((e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking)) != cudaSuccess) return bail(e);
+    int64_t off = 0;
+    for (int l = 0; l < kLayers; ++l) {
+        h->L.w_off[l] = off;
+        off += int64_t(layer_in(l)) * layer_out(l);
+        h->L.b_off[l] = off;
+        off += layer_out(l);
+        if ((e = alloc(h, &h->L.W[l], int64_t(layer_in(l)) * layer_out(l))) != cudaSuccess) return bail(e);
+    }
+    if ((e = alloc(h, &h->p, h->nparam)) != cudaSuccess || (e = alloc(h, &h->g, h->nparam)) != cudaSuccess ||
+        (e = alloc(h, &h->m, h->nparam)) != cudaSuccess || (e = alloc(h, &h->v, h->nparam)) != cudaSuccess ||
+        (e = alloc(h, &h->proj, 16)) != cudaSuccess || (e = alloc(h, &h->dA, capacity * kWidth)) != cudaSuccess ||
+        (e = alloc(h, &h->dZ, capacity * kWidth)) != cudaSuccess ||
+        (e = alloc(h, &h->dZb, capacity * kWidth)) != cudaSuccess ||
+        (e = alloc(h, &h->partial, int64_t(blocks(capacity * kOut, 256)))) != cudaSuccess ||
+        (e = alloc(h, &h->loss_dev, 1)) != cudaSuccess)
+        return bail(e);
+    for (int l = 0; l <= kLayers; ++l) {
+        const int w = l == 0 ? kIn : (l == kLayers ? kOut : kWidth);
+        if ((e = alloc(h, &h->Af[l], capacity * w)) != cudaSuccess ||
+            (e = alloc(h, &h->Ab[l], capacity * w)) != cudaSuccess)
+            return bail(e);
+    }
+    if ((e = cudaMemcpy(h->proj, proj, 16 * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemset(h->p, 0, sizeof(float) * h->nparam)) != cudaSuccess ||
+        (e = cudaMemset(h->m, 0, sizeof(float) * h->nparam)) != cudaSuccess ||
+        (e = cudaMemset(h->v, 0, sizeof(float) * h->nparam)) != cudaSuccess)
+        return bail(e);
+    *out = h;
+    return LSKUM_OK;
+}
+
+void lskum_mlp_destroy(lskum_mlp* h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    for (void* p : h->allocs) cudaFree(p);
+    cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+int lskum_mlp_set_params(lskum_mlp* h, const float* params, int64_t n) {
+    if (!h || !params || n != h->nparam) return fail(LSKUM_ERR_INVALID_ARG, "lskum_mlp_set_params: size");
+    MLP_CUDA(cudaMemcpyAsync(h->p, params, sizeof(float) * n, cudaMemcpyHostToDevice, h->stream));
+    MLP_CUDA(cudaMemsetAsync(h->m, 0, sizeof(float) * n, h->stream));
+    MLP_CUDA(cudaMemsetAsync(h->v, 0, sizeof(float) * n, h->stream));
+    h->step = 0;
+    MLP_CUDA((k_weights_bf16<<<dim3(blocks(int64_t(kWidth) * kWidth, 256), kLayers), 256, 0, h->stream>>>(h->p, h->L),
+              cudaGetLastError()));
+    MLP_CUDA(cudaStreamSynchronize(h->stream));
+    return LSKUM_OK;
+}
+
+int lskum_mlp_get_params(lskum_mlp* h, float* params, int64_t n) {
+    if (!h || !params || n != h->nparam) return fail(LSKUM_ERR_INVALID_ARG, "lskum_mlp_get_params: size");
+    MLP_CUDA(cudaMemcpyAsync(params, h->p, sizeof(float) * n, cudaMemcpyDeviceToHost, h->stream));
+    MLP_CUDA(cudaStreamSynchronize(h->stream));
+    return LSKUM_OK;
+}
+
+int lskum_mlp_features(lskum_mlp* h, const float* raw, int64_t n, float* feat) {
+    if (!h || !raw || !feat) return fail(LSKUM_ERR_INVALID_ARG, "lskum_mlp_features: null");
+    if (n < 1) return fail(LSKUM_ERR_INVALID_ARG, "lskum_mlp_features: n < 1");
+    MLP_CUDA((k_features<<<blocks(n, 256), 256, 0, h->stream>>>(raw, n, h->proj, feat), cudaGetLastError()));
+    MLP_CUDA(cudaStreamSynchronize(h->stream));
+    return LSKUM_OK;
+}
+
+int lskum_mlp_predict(lskum_mlp* h, const float* feat, int64_t n, float* out) {
+    if (!h || !feat || !out) return fail(LSKUM_ERR_INVALID_ARG, "lskum_mlp_predict: null");
+    int rc = check_n(h, n);
+    if (rc) return rc;
+    MLP_CUDA(cudaMemcpyAsync(h->Af[0], feat, sizeof(float) * n * kIn, cudaMemcpyDeviceToDevice, h->stream));
+    rc = forward(h, n);
+    if (rc) return rc;
+    MLP_CUDA(cudaMemcpyAsync(out, h->Af[kLayers], sizeof(float) * n * kOut, cudaMemcpyDeviceToDevice, h->stream));
+    MLP_CUDA(cudaStreamSynchronize(h->stream));
+    return LSKUM_OK;
+}
+
+int lskum_mlp_gradients(lskum_mlp* h, const float* feat, const float* target, int64_t n, float* grads,
+                        double* loss) {
+    if (!h || !feat || !target) return fail(LSKUM_ERR_INVALID_ARG, "lskum_mlp_gradients: null");
+    int rc = check_n(h, n);
+    if (rc) return rc;
+    MLP_CUDA(cudaMemcpyAsync(h->Af[0], feat, sizeof(float) * n * kIn, cudaMemcpyDeviceToDevice, h->stream));
+    if ((rc = forward(h, n)) || (rc = backward(h, target, n))) return rc;
+    if (grads) MLP_CUDA(cudaMemcpyAsync(grads, h->g, sizeof(float) * h->nparam, cudaMemcpyDeviceToHost, h->stream));
+    if (loss) MLP_CUDA(cudaMemcpyAsync(loss, h->loss_dev, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    MLP_CUDA(cudaStreamSynchronize(h->stream));
+    return LSKUM_OK;
+}
+
+int lskum_mlp_train_step(lskum_mlp* h, const float* feat, const float* target, int64_t n, float lr,
+                         double* loss) {
+    if (!h || !feat || !target || !(lr > 0.f)) return fail(LSKUM_ERR_INVALID_ARG, "lskum_mlp_train_step: argument");
+    int rc = check_n(h, n);
+    if (rc) return rc;
+    MLP_CUDA(cudaMemcpyAsync(h->Af[0], feat, sizeof(float) * n * kIn, cudaMemcpyDeviceToDevice, h->stream));
+    if ((rc = forward(h, n)) || (rc = backward(h, target, n))) return rc;
+    h->step += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f / (1.f - powf(b1, float(h->step)));
+    const float c2 = 1.f / (1.f - powf(b2, float(h->step)));
+    MLP_CUDA((k_adam<<<blocks(h->nparam, 256), 256, 0, h->stream>>>(h->p, h->g, h->m, h->v, h->nparam, lr, b1, b2,
+                                                                     1e-8f, c1, c2),
+              cudaGetLastError()));
+    MLP_CUDA((k_weights_bf16<<<dim3(blocks(int64_t(kWidth) * kWidth, 256), kLayers), 256, 0, h->stream>>>(h->p, h->L),
+              cudaGetLastError()));
+    if (loss) {
+        MLP_CUDA(cudaMemcpyAsync(loss, h->loss_dev, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        MLP_CUDA(cudaStreamSynchronize(h->stream));
+    }
+    return LSKUM_OK;
+}
+
+int lskum_mlp_sync(lskum_mlp* h) {
+    if (!h) return fail(LSKUM_ERR_INVALID_ARG, "null");
+    MLP_CUDA(cudaStreamSynchronize(h->stream));
+    return LSKUM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,131 @@
+"""Warm-start study: train the surrogate on converged solutions from the
+batched solver and measure what it gains over the free-stream start.
+
+  python -m paper_2108_07031_gb300.warmstart_study [--out results.json]
+
+Cloud: the 5,120-point NACA 0012 cloud (128 x 40). Training: 256 seeded
+conditions, M ~ U[0.3, 0.8], alpha ~ U[-4, 6] deg, each solved by the
+batched mixed-precision solver (64 conditions per launch, CFL 0.8: the
+converged state does not depend on the pseudo-time step) to a 7-order
+residue drop. Network: the 6-layer, width-256 BF16 tensor-core MLP, Adam with
+a cosine schedule. Evaluation: 32 held-out conditions (another seed), each
+solved from the free stream and from the network's prediction at the
+configuration's CFL 0.2; reported: iterations until the residue is 1e-6 of
+the free-stream start's first residue, and the converged Cl/Cd of both.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+
+def main():
+    import torch
+
+    from . import cloud as Cl
+    from . import lskum as L
+    from . import surrogate as S
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--out", default="warmstart_study.json")
+    ap.add_argument("--train", type=int, default=256)
+    ap.add_argument("--test", type=int, default=32)
+    ap.add_argument("--epochs", type=int, default=80)
+    ap.add_argument("--eval-cfl", type=float, default=0.2)
+    ap.add_argument("--eval-iters", type=int, default=60_000)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    args = ap.parse_args()
+    prec = L.MIXED if args.precision == "mixed" else L.FP64
+    log = lambda m: print(m, flush=True)  # noqa: E731
+
+    cloud = Cl.naca0012_cloud(128, 40)
+    wd = S.wall_distance(cloud)
+    m_tr, a_tr = Cl.conditions(args.train, seed=2021)
+    m_te, a_te = Cl.conditions(args.test, seed=4242)
+    t0 = time.time()
+    W_tr, it_tr = S.converged_solutions(cloud, m_tr, a_tr, tol=1e-7, max_iters=40_000)
+    t_data = time.time() - t0
+    log(f"training data: {args.train} conditions in {t_data:.1f} s (iterations per batch {it_tr})")
+
+    raw = np.concatenate(S.raw_inputs(cloud, wd, m_tr, a_tr))
+    T = np.concatenate([S.targets(W_tr[k], m_tr[k], a_tr[k]) for k in range(args.train)])
+    net = S.MLP(capacity=16384, seed=0)
+    feats = net.features(torch.from_numpy(raw).cuda())
+    Td = torch.from_numpy(T).cuda()
+    t0 = time.time()
+    losses = S.train(net, feats, Td, epochs=args.epochs, batch=8192, lr=2e-3, lr_final=2e-5,
+                     log=log)
+    t_train = time.time() - t0
+
+    # held-out: both starts in one batched solve each (32 conditions)
+    n = args.test
+    nc = 1 << int(np.ceil(np.log2(n)))
+    pred, fallback = [], 0
+    for k in range(n):
+        W = S.predict_state(net, cloud, wd, m_te[k], a_te[k])
+        if W is None:
+            fallback += 1
+            W = np.tile(S.freestream(m_te[k], a_te[k]), (cloud.n, 1))
+        pred.append(W)
+    # prediction error against the reference solutions computed below
+    results = {}
+    chunk = 100
+    for mode in ("cold", "warm"):
+        with L.Solver.from_cloud(cloud, precision=prec, cfl=args.eval_cfl, n_conditions=nc) as s:
+            mm = np.concatenate([m_te, np.repeat(m_te[-1:], nc - n)])
+            aa = np.concatenate([a_te, np.repeat(a_te[-1:], nc - n)])
+            s.set_conditions(mm, aa)
+            if mode == "cold":
+                s.step(2)
+                r_first = s.residual_norm()[:n].copy()
+                s.set_conditions(mm, aa)
+            else:
+                W0 = np.concatenate([np.stack(pred), np.repeat(np.stack(pred)[-1:], nc - n, 0)])
+                s.set_state(W0)
+            hist = []
+            t0 = time.time()
+            for _ in range(args.eval_iters // chunk):
+                s.step(chunk)
+                hist.append(s.residual_norm()[:n].copy())
+            cl, cd = s.forces()
+            W_end = s.get_state()[:n]
+            results[mode] = {"hist": np.array(hist), "cl": cl[:n], "cd": cd[:n], "W": W_end,
+                             "time": time.time() - t0}
+    thr = 1e-6 * r_first
+    def first_below(h):
+        ok = h < thr[None, :]
+        return np.where(ok.any(0), chunk * (1 + ok.argmax(0)), -1)
+    it_cold = first_below(results["cold"]["hist"])
+    it_warm = first_below(results["warm"]["hist"])
+    both = (it_cold > 0) & (it_warm > 0)
+    saving = 1 - it_warm[both] / it_cold[both]
+    pred_err = [float(np.abs(pred[k] - results["cold"]["W"][k]).max() /
+                      np.abs(results["cold"]["W"][k]).max()) for k in range(n)]
+    out = {
+        "cloud_points": cloud.n, "train_conditions": args.train, "test_conditions": n,
+        "eval_cfl": args.eval_cfl, "precision": args.precision,
+        "data_seconds": t_data, "train_seconds": t_train,
+        "loss_first": losses[0], "loss_last": losses[-1], "fallbacks": fallback,
+        "iterations_cold": it_cold.tolist(), "iterations_warm": it_warm.tolist(),
+        "converged_both": int(both.sum()),
+        "saving_mean": float(saving.mean()) if saving.size else None,
+        "saving_median": float(np.median(saving)) if saving.size else None,
+        "saving_min": float(saving.min()) if saving.size else None,
+        "cl_cold": results["cold"]["cl"].tolist(), "cl_warm": results["warm"]["cl"].tolist(),
+        "cd_cold": results["cold"]["cd"].tolist(), "cd_warm": results["warm"]["cd"].tolist(),
+        "dcl_abs_mean": float(np.mean(np.abs(results["warm"]["cl"] - results["cold"]["cl"]))),
+        "dcd_abs_mean": float(np.mean(np.abs(results["warm"]["cd"] - results["cold"]["cd"]))),
+        "prediction_rel_err_max_mean": float(np.mean(pred_err)),
+        "mach": m_te.tolist(), "alpha": a_te.tolist(),
+    }
+    with open(args.out, "w") as f:
+        json.dump(out, f, indent=1)
+    log(json.dumps({k: v for k, v in out.items() if not isinstance(v, list)}))
+
+
+if __name__ == "__main__":
+    main()
