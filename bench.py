@@ -158,12 +158,15 @@ def _fp64_peak():
 
 # Per-unit figures of the FP64 flux/update kernel (k_flux), from one ncu
 # capture of a stage launch on the 600,138-point cloud (8,338,298 neighbour
-# entries): 54,445,637 fused and 40,788,614 non-fused FP64 warp instructions
-# = 4.79e9 FP64 flops = 574.4 flops per neighbour entry, and 439.0 MB of DRAM
-# traffic = 731.5 bytes per point. Units of one launch: neighbour entries
-# (flops) and points (bytes); both scale in proportion with the cloud size.
-FLUX_FP64_FLOPS_PER_NEIGHBOUR = 574.4
-FLUX_DRAM_BYTES_PER_POINT = 731.5
+# entries): 1.342e9 DFMA, 0.279e9 DADD and 1.035e9 DMUL thread instructions
+# (predicated on) = 4.00e9 FP64 flops = 479.4 flops per neighbour entry, and
+# 438.2 MB of DRAM traffic = 730.2 bytes per point. Units of one launch:
+# neighbour entries (flops) and points (bytes); both scale in proportion with
+# the cloud size. With this instruction mix a saturated FP64 pipe reaches
+# (2 DFMA + DADD + DMUL) / (2 (DFMA + DADD + DMUL)) = 0.753 of the FMA peak.
+FLUX_FP64_FLOPS_PER_NEIGHBOUR = 479.4
+FLUX_DRAM_BYTES_PER_POINT = 730.2
+FLUX_FRAC_CEILING = 0.753
 ALGORITHMIC_BYTES_PER_POINT_ITERATION = 4600.0  # minimal passes, gathers from cache
 
 
@@ -274,6 +277,7 @@ def run_ours(args, rank, world, local):
                 "peak_source": "FP64 FMA rate measured live by pipe_peaks on this GPU "
                                "(nominal 1.25 TFLOP/s)",
                 "flops_per_launch": FLUX_FP64_FLOPS_PER_NEIGHBOUR * nnz,
+                "frac_ceiling_at_instruction_mix": FLUX_FRAC_CEILING,
                 "launch_ms": flux_launch_ms,
                 "traffic_note": "ncu dram bytes of a 0.6M-point launch scaled by points",
                 "hbm_frac_of_measured_whole_step":
@@ -304,6 +308,10 @@ def run_ours(args, rank, world, local):
         variants["batched64_fp64"] = time_variant(
             args, c06, L.FP64, 64, stream, barrier, dist,
             "the same 64 conditions in FP64", conditions=(mach, alpha), autotune=True)
+        variants["fp64_split_flux_ablation"] = time_variant(
+            args, cloud, L.FP64, 1, stream, barrier, dist,
+            "10M-point cloud, FP64, the paper's kernel splitting (four split-flux kernels "
+            "and a stage kernel per stage)", split=True)
         packed, sizes = _ragged_cloud()
         variants["ragged16_mixed"] = time_variant(
             args, packed, L.MIXED, 1, stream, barrier, dist,
@@ -328,13 +336,14 @@ def _ragged_cloud():
 
 
 def time_variant(args, cloud, precision, n_cond, stream, barrier, dist, what,
-                 conditions=None, autotune=False):
+                 conditions=None, autotune=False, split=False):
     """Same timed region as the headline for another precision / batch shape."""
     import torch
 
     from paper_2108_07031_gb300 import cloud as Cl
     from paper_2108_07031_gb300 import lskum as L
-    s = L.Solver.from_cloud(cloud, precision=precision, n_conditions=n_cond)
+    s = L.Solver.from_cloud(cloud, precision=precision, n_conditions=n_cond,
+                            flux_split=1 if split else 0)
     s.set_stream(stream.cuda_stream)
     if conditions is None:
         s.set_freestream(MACH, ALPHA)

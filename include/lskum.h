@@ -85,6 +85,10 @@ typedef struct {
                            device; every per-point host array below then holds n_conditions
                            blocks of n points (condition-major), and per-run outputs
                            (residue, Cl, Cd) hold n_conditions values. */
+    int flux_split;     /* 0 (default): one fused flux/update kernel per stage. 1: the paper's
+                           kernel splitting (Section 5): one kernel per split-flux derivative
+                           (dGs+/ds, dGs-/ds, dGn+/dn, dGn-/dn) and one stage-update kernel;
+                           an ablation, FP64 only. */
 } lskum_options;
 
 /* Fills *o with the defaults listed above. Returns LSKUM_ERR_INVALID_ARG if o is NULL. */

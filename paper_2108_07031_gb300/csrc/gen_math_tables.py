@@ -1,4 +1,6 @@
-"""Writes ``erfc_tables.h``: polynomial pieces for the split-flux erfc.
+"""Writes ``math_tables.h``: the FP64 flux kernel's function tables.
+
+1. Polynomial pieces for the split-flux erfc.
 
 The kinetic split fluxes need A = erfc(x) / 2 and B ~ exp(-x^2) at the same
 argument. The device code evaluates
@@ -13,7 +15,12 @@ variable; the script checks the relative error of every piece at 2000 points
 in double-precision Horner evaluation and refuses to write the header unless
 it is below 4e-16.
 
-Run: python gen_erfc_tables.py  (writes erfc_tables.h next to this file)
+2. The exponential by Tang's table-driven method: x = k ln2/64 + r with
+|r| <= ln2/128, exp(x) = 2^(k div 64) * 2^((k mod 64)/64) * e^r; the table
+holds 2^(j/64), j < 64, correctly rounded (mpmath), and ln2/64 is split into
+a double and its remainder for an exact reduction.
+
+Run: python gen_math_tables.py  (writes math_tables.h next to this file)
 """
 
 import os
@@ -84,9 +91,14 @@ def main():
         pieces.append([float(x) for x in C])
         a = hi
 
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "erfc_tables.h")
+    # 2^(j/64) and the split of ln2/64
+    tab = [float(mp.mpf(2) ** (mp.mpf(j) / 64)) for j in range(64)]
+    ln2_64 = mp.log(2) / 64
+    hi = float(ln2_64)
+    lo = float(ln2_64 - mp.mpf(hi))
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "math_tables.h")
     with open(path, "w") as f:
-        f.write("// Generated by gen_erfc_tables.py -- do not edit.\n")
+        f.write("// Generated by gen_math_tables.py -- do not edit.\n")
         f.write("// Chebyshev interpolants (mpmath, 50 digits) of erf(x)/x in x^2 on [0, 1/4] and of\n")
         f.write("// erfcx(a) = exp(a^2) erfc(a) in (a - c_k) on 1/4-wide intervals of [0.5, 6].\n")
         f.write(f"// Max relative error in double Horner: erf {out[0][2]:.2e}, erfcx {worst:.2e}.\n")
@@ -102,6 +114,14 @@ def main():
         f.write("__device__ const double kErfcxC[kErfcxPieces][kErfcxDeg + 2] = {\n")
         for c, p in zip(centres, pieces):
             f.write("    {" + f"{c!r}, " + ", ".join(repr(x) for x in p) + "},\n")
+        f.write("};\n\n")
+        f.write("// exp(x) by Tang's table-driven reduction: 2^(j/64), j < 64, correctly rounded,\n")
+        f.write("// and ln2/64 = kLn2By64Hi + kLn2By64Lo.\n")
+        f.write(f"constexpr double kLn2By64Hi = {hi!r};\nconstexpr double kLn2By64Lo = {lo!r};\n")
+        f.write(f"constexpr double kInvLn2By64 = {float(1 / ln2_64)!r};\n")
+        f.write("__device__ const double kExp2Tab[64] = {\n")
+        for j in range(0, 64, 4):
+            f.write("    " + ", ".join(repr(v) for v in tab[j:j + 4]) + ",\n")
         f.write("};\n\n}  // namespace lskum\n")
     print(f"wrote {path}: erf err {out[0][2]:.2e}, erfcx worst {worst:.2e}, {len(pieces)} pieces")
 

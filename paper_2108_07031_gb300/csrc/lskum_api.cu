@@ -168,6 +168,9 @@ cudaError_t launch_flux_any(lskum_ctx* c, int mode, int qb, int dbuf, int qout) 
     if (c->mixed)
         return launch_flux_mx(mode, c->g, c->g32, c->ph, c->st, c->st.qhl[qb], c->st.dq32[dbuf],
                               qout >= 0 ? c->st.qhl[qout] : nullptr, c->block, c->stream);
+    if (c->opt.flux_split)
+        return launch_flux_split(mode, c->g, c->ph, c->st, c->st.q[qb], c->st.dq[dbuf],
+                                 qout >= 0 ? c->st.q[qout] : nullptr, c->block, c->stream);
     return launch_flux(mode, c->g, c->ph, c->st, c->st.q[qb], c->st.dq[dbuf],
                        qout >= 0 ? c->st.q[qout] : nullptr, c->block, c->stream);
 }
@@ -182,7 +185,7 @@ cudaError_t run_iteration(lskum_ctx* c, int64_t* launches) {
         if (e != cudaSuccess) return e;
         e = timed(c, kFlux, [&] { return launch_flux_any(c, stage, qcur, dbuf, 1 - qcur); });
         if (e != cudaSuccess) return e;
-        ++*launches;
+        *launches += c->opt.flux_split ? 5 : 1;
         qcur = 1 - qcur;
         if (stage == 1) {
             e = timed(c, kReduce, [&] {
@@ -253,6 +256,7 @@ int lskum_default_options(lskum_options* o) {
     o->block_size = 0;
     o->check_every = 50;
     o->n_conditions = 1;
+    o->flux_split = 0;
     return LSKUM_OK;
 }
 
@@ -269,7 +273,8 @@ int lskum_create(int64_t n, const double* xy, const double* normals, const int8_
         (o.outer_mode != 0 && o.outer_mode != 1) ||
         (o.precision != LSKUM_FP64 && o.precision != LSKUM_MIXED) ||
         (o.block_size != 0 && o.block_size != 128 && o.block_size != 256) || o.check_every < 1 ||
-        o.n_conditions < 1 || o.n_conditions > 256 || (o.n_conditions & (o.n_conditions - 1)))
+        o.n_conditions < 1 || o.n_conditions > 256 || (o.n_conditions & (o.n_conditions - 1)) ||
+        (o.flux_split != 0 && o.flux_split != 1) || (o.flux_split && o.precision != LSKUM_FP64))
         return fail(LSKUM_ERR_INVALID_ARG, "invalid option value");
 
     lskum_ctx* c = new (std::nothrow) lskum_ctx();
@@ -496,7 +501,7 @@ int lskum_step(lskum_ctx* c, int n_iters) {
     for (int it = 0; it < n_iters; ++it) {
         if (graph) {
             LSKUM_CUDA(cudaGraphLaunch(c->graph_exec, c->stream));
-            launches += 4 * (2 + c->opt.inner_iters) + (c->C == 1 ? 1 : 2);
+            launches += 4 * (1 + c->opt.inner_iters + (c->opt.flux_split ? 5 : 1)) + (c->C == 1 ? 1 : 2);
         } else {
             cudaError_t e = run_iteration(c, &launches);
             if (e != cudaSuccess) return cuda_fail(e, "iteration launch");

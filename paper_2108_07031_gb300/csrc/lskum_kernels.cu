@@ -25,7 +25,7 @@
 #include <cmath>
 
 #include "lskum_internal.h"
-#include "erfc_tables.h"
+#include "math_tables.h"
 #include "lskum_kernels.cuh"
 
 namespace lskum {
@@ -40,6 +40,25 @@ struct Prim {
     double r, u, v, p, sb, isb;  // density, velocity (frame components), pressure, sqrt(beta), 1/sqrt(beta)
 };
 
+// exp(x) by Tang's table-driven method (math_tables.h): x = k ln2/64 + r,
+// |r| <= ln2/128, exp(x) = 2^(k>>6) 2^((k&63)/64) e^r with e^r - 1 from its
+// degree-6 Taylor polynomial (remainder < 3e-20): about 11 FP64 operations
+// against the library's ~18. Outside |x| <= 700 the library exp (the scaling
+// below stays in the normal range inside it).
+__device__ __forceinline__ double exp_tab(const double x) {
+    if (!(fabs(x) <= 700.0)) return exp(x);
+    const double shifter = 6755399441055744.0;  // 1.5 * 2^52: rounds k into the low bits
+    double kd = fma(x, kInvLn2By64, shifter);
+    const int64_t k = __double_as_longlong(kd) - 0x4338000000000000LL;
+    kd -= shifter;
+    const double r = fma(-kd, kLn2By64Lo, fma(-kd, kLn2By64Hi, x));
+    const double p =
+        r * fma(r, fma(r, fma(r, fma(r, fma(r, 1.0 / 720.0, 1.0 / 120.0), 1.0 / 24.0), 1.0 / 6.0), 0.5), 1.0);
+    const double t = kExp2Tab[k & 63];
+    const double res = fma(t, p, t);
+    return __longlong_as_double(__double_as_longlong(res) + ((k >> 6) << 52));
+}
+
 // q -> primitive (inverse of Eq. 26); velocities in the global frame. With
 // gamma = 1.4 (1/(gamma-1) = 5/2) the factor beta^(-1/(gamma-1)) of the
 // density is (1/sqrt(beta))^5, so no logarithm is needed; 1/sqrt(beta) is
@@ -49,17 +68,17 @@ __device__ __forceinline__ Prim q_to_prim(const double t0, const double t1, cons
                                           const double t3, const double gm1_inv) {
     Prim w;
     const double beta = -0.5 * t3;
-    const double inv2b = -1.0 / t3;  // 1 / (2 beta)
-    w.u = t1 * inv2b;
-    w.v = t2 * inv2b;
     w.isb = rsqrt(beta);
     w.sb = beta * w.isb;
+    const double i2 = w.isb * w.isb;  // 1 / beta
+    const double inv2b = 0.5 * i2;    // 1 / (2 beta)
+    w.u = t1 * inv2b;
+    w.v = t2 * inv2b;
     const double uu = w.u * w.u + w.v * w.v;
     if (G14) {
-        const double i2 = w.isb * w.isb;
-        w.r = exp(t0 + beta * uu) * (i2 * i2 * w.isb);
+        w.r = exp_tab(t0 + beta * uu) * (i2 * i2 * w.isb);
     } else {
-        w.r = exp(t0 - log(beta) * gm1_inv + beta * uu);
+        w.r = exp_tab(t0 - log(beta) * gm1_inv + beta * uu);
     }
     w.p = w.r * inv2b;
     return w;
@@ -67,7 +86,7 @@ __device__ __forceinline__ Prim q_to_prim(const double t0, const double t1, cons
 
 // erfc(x) / 2 given e = exp(-x^2): erf(x) = x P(x^2) for |x| <= 0.5, and
 // erfc(|x|) = e erfcx(|x|) on [0.5, 6] from the piecewise polynomials of
-// erfc_tables.h (the exponential is shared with the split flux's B term);
+// math_tables.h (the exponential is shared with the split flux's B term);
 // beyond 6 the library erfc (where erfc < 2e-17).
 __device__ __forceinline__ double half_erfc(const double x, const double e) {
     const double a = fabs(x);
@@ -100,7 +119,7 @@ __device__ __forceinline__ void split_flux_a(const double r, const double ua, co
                                              const double p, const double sb, const double isb,
                                              const double sg, const double gm1_inv, double g[4]) {
     const double S = ua * sb;
-    const double e = exp(-S * S);
+    const double e = exp_tab(-S * S);
     const double A = half_erfc(-sg * S, e);
     const double B = (0.5 * kInvSqrtPi) * e * isb;
     const double rhoe = p * gm1_inv + 0.5 * r * (ua * ua + ub * ub);
@@ -218,6 +237,64 @@ __global__ void __launch_bounds__(BLOCK) k_ls_inner(const DevGeom g, const V4* _
 
 // ------------------------------------------------------- flux residual + RK
 
+// SSP-RK stage epilogue of one (point, condition), shared by the fused flux
+// kernel and the split-flux ablation: mode 0 stores R; modes 1..4 apply the
+// stage update, the wall condition and the next q; stage 1 also stores dt
+// and U0 and returns R_rho^2 for the residue.
+template <int MODE>
+__device__ __forceinline__ double stage_epilogue(const DevGeom& g, const Physics& ph,
+                                                 const DevState& st, const int64_t t,
+                                                 const int64_t d, const int8_t fl, const bool fixed,
+                                                 const double R[4], V4* __restrict__ q_out) {
+    double r2 = 0.0;
+    if (MODE == 0) {
+        st.R[t] = V4{R[0], R[1], R[2], R[3]};
+    } else {
+        V4 U = ld4(st.U + t);
+        double dtv;
+        if (MODE == 1) {
+            const double rho = U.a, u = U.b / rho, v = U.c / rho;
+            const double p = ph.gm1 * (U.d - 0.5 * rho * (u * u + v * v));
+            dtv = ph.cfl * g.dmin[d] / (sqrt(u * u + v * v) + sqrt(ph.gamma * p / rho));
+            st.dt[t] = dtv;
+            st.U0[t] = U;
+            r2 = R[0] * R[0];
+        } else {
+            dtv = st.dt[t];
+        }
+        if (!fixed) {
+            const double h = 0.5 * dtv;
+            if (MODE == 3) {
+                const V4 U0 = ld4(st.U0 + t);
+                U.a = (2.0 / 3.0) * U0.a + (1.0 / 3.0) * (U.a - h * R[0]);
+                U.b = (2.0 / 3.0) * U0.b + (1.0 / 3.0) * (U.b - h * R[1]);
+                U.c = (2.0 / 3.0) * U0.c + (1.0 / 3.0) * (U.c - h * R[2]);
+                U.d = (2.0 / 3.0) * U0.d + (1.0 / 3.0) * (U.d - h * R[3]);
+            } else {
+                U.a -= h * R[0];
+                U.b -= h * R[1];
+                U.c -= h * R[2];
+                U.d -= h * R[3];
+            }
+            if (fl == LSKUM_WALL) {  // remove the wall-normal momentum
+                const double2 nn = g.nrm[d];
+                const double tx = nn.y, ty = -nn.x;
+                const double ms = U.b * tx + U.c * ty;
+                U.b = ms * tx;
+                U.c = ms * ty;
+            }
+            st.U[t] = U;
+        }
+        V4 qn;
+        double rho, u, v, p;
+        cons_to_q(U, ph, qn, rho, u, v, p);
+        q_out[t] = qn;
+        if (!physical(rho, u, v, p)) atomicOr(st.status, 1);
+    }
+
+    return r2;
+}
+
 template <int MODE, int BLOCK, bool G14>
 __global__ void __launch_bounds__(BLOCK) k_flux(const DevGeom g, const Physics ph,
                                                 const DevState st, const V4* __restrict__ q_in,
@@ -305,56 +382,145 @@ __global__ void __launch_bounds__(BLOCK) k_flux(const DevGeom g, const Physics p
                 R[2] = rs * ty + rn * ny;
             }
         }
-        if (MODE == 0) {
-            st.R[t] = V4{R[0], R[1], R[2], R[3]};
-        } else {
-            V4 U = ld4(st.U + t);
-            double dtv;
-            if (MODE == 1) {
-                const double rho = U.a, u = U.b / rho, v = U.c / rho;
-                const double p = ph.gm1 * (U.d - 0.5 * rho * (u * u + v * v));
-                dtv = ph.cfl * g.dmin[d] / (sqrt(u * u + v * v) + sqrt(ph.gamma * p / rho));
-                st.dt[t] = dtv;
-                st.U0[t] = U;
-                r2 = R[0] * R[0];
-            } else {
-                dtv = st.dt[t];
-            }
-            if (!fixed) {
-                const double h = 0.5 * dtv;
-                if (MODE == 3) {
-                    const V4 U0 = ld4(st.U0 + t);
-                    U.a = (2.0 / 3.0) * U0.a + (1.0 / 3.0) * (U.a - h * R[0]);
-                    U.b = (2.0 / 3.0) * U0.b + (1.0 / 3.0) * (U.b - h * R[1]);
-                    U.c = (2.0 / 3.0) * U0.c + (1.0 / 3.0) * (U.c - h * R[2]);
-                    U.d = (2.0 / 3.0) * U0.d + (1.0 / 3.0) * (U.d - h * R[3]);
-                } else {
-                    U.a -= h * R[0];
-                    U.b -= h * R[1];
-                    U.c -= h * R[2];
-                    U.d -= h * R[3];
-                }
-                if (fl == LSKUM_WALL) {  // remove the wall-normal momentum
-                    const double2 nn = g.nrm[d];
-                    const double tx = nn.y, ty = -nn.x;
-                    const double ms = U.b * tx + U.c * ty;
-                    U.b = ms * tx;
-                    U.c = ms * ty;
-                }
-                st.U[t] = U;
-            }
-            V4 qn;
-            double rho, u, v, p;
-            cons_to_q(U, ph, qn, rho, u, v, p);
-            q_out[t] = qn;
-            if (!physical(rho, u, v, p)) atomicOr(st.status, 1);
-        }
+        r2 = stage_epilogue<MODE>(g, ph, st, t, d, fl, fixed, R, q_out);
     }
     if (MODE == 1) {
         if (g.cshift == 0) {  // one condition: fused block partial sums
             const double s = block_sum<BLOCK>(r2);
             if (threadIdx.x == 0) st.partials[blockIdx.x] = s;
         } else if (d < g.n) {  // several: per (point, condition), reduced per condition
+            st.r2[t] = r2;
+        }
+    }
+}
+
+// ------------------------------------------------ split-flux kernels (ablation)
+// The paper's kernel splitting (Section 5, the four split-flux kernels Gx+,
+// Gx-, Gy+, Gy-): one kernel per split-flux derivative dGs+/ds, dGs-/ds,
+// dGn+/dn, dGn-/dn, each adding its stencil's contribution to the residual
+// (local frame) in Racc, then one kernel for the stage update. An ablation of
+// the fused kernel: a neighbour's two q~ -> primitive maps are computed once
+// per stencil it belongs to (twice), and Racc makes four extra round trips.
+template <int PART, int BLOCK, bool G14>
+__global__ void __launch_bounds__(BLOCK) k_flux_part(const DevGeom g, const Physics ph,
+                                                     const V4* __restrict__ q_in,
+                                                     const V8* __restrict__ dq,
+                                                     V4* __restrict__ Racc) {
+    const int64_t t = int64_t(blockIdx.x) * BLOCK + threadIdx.x;
+    const int64_t d = t >> g.cshift;
+    const uint32_t cc = uint32_t(t) & g.cmask;
+    if (d >= g.n) return;
+    const int8_t fl = g.flag[d];
+    double R[4] = {0.0, 0.0, 0.0, 0.0};
+    if (!(ph.outer_fixed && fl == LSKUM_OUTER)) {
+        double tx = 1.0, ty = 0.0, nx = 0.0, ny = 1.0;
+        const bool local = fl != LSKUM_INTERIOR;
+        if (local) {
+            const double2 nn = g.nrm[d];
+            nx = nn.x;
+            ny = nn.y;
+            tx = ny;
+            ty = -nx;
+        }
+        const V4 qi = ld4(q_in + t);
+        const V8 di = dq[t];
+        const double qiv[4] = {qi.a, qi.b, qi.c, qi.d};
+        const bool second = ph.order == 2;
+        const uint32_t want = (PART % 2 == 0) ? 1u : 2u;
+        const double sg = (PART % 2 == 0) ? 1.0 : -1.0;
+        const int c = g.cnt[d];
+        for (int k = 0; k < c; ++k) {
+            const int64_t at = int64_t(k) * g.stride + d;
+            const uint32_t e = g.nbr[at];
+            const uint32_t code = PART < 2 ? ((e >> kIndexBits) & 3u) : ((e >> (kIndexBits + 2)) & 3u);
+            if (code != want) continue;
+            const uint32_t j = e & kIndexMask;
+            const int64_t jt = sidx(g, j, cc);
+            const V4 qj = ld4(q_in + jt);
+            double tj[4] = {qj.a, qj.b, qj.c, qj.d};
+            double t0[4] = {qiv[0], qiv[1], qiv[2], qiv[3]};
+            if (second) {
+                const double hx = g.hdx[at], hy = g.hdy[at];
+                const V8 dj = dq[jt];
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    tj[m] = tj[m] - (hx * dj.x[m] + hy * dj.y[m]);
+                    t0[m] = t0[m] - (hx * di.x[m] + hy * di.y[m]);
+                }
+            }
+            if (tj[0] == t0[0] && tj[1] == t0[1] && tj[2] == t0[2] && tj[3] == t0[3]) continue;
+            Prim wj = q_to_prim<G14>(tj[0], tj[1], tj[2], tj[3], ph.gm1_inv);
+            Prim w0 = q_to_prim<G14>(t0[0], t0[1], t0[2], t0[3], ph.gm1_inv);
+            if (local) {
+                const double sj = wj.u * tx + wj.v * ty, nj = wj.u * nx + wj.v * ny;
+                const double s0 = w0.u * tx + w0.v * ty, n0 = w0.u * nx + w0.v * ny;
+                wj.u = sj; wj.v = nj;
+                w0.u = s0; w0.v = n0;
+            }
+            double gj[4], g0[4];
+            if (PART < 2) {
+                split_flux_a(wj.r, wj.u, wj.v, wj.p, wj.sb, wj.isb, sg, ph.gm1_inv, gj);
+                split_flux_a(w0.r, w0.u, w0.v, w0.p, w0.sb, w0.isb, sg, ph.gm1_inv, g0);
+                const double w = g.ws[at];
+                R[0] += w * (gj[0] - g0[0]);
+                R[1] += w * (gj[1] - g0[1]);
+                R[2] += w * (gj[2] - g0[2]);
+                R[3] += w * (gj[3] - g0[3]);
+            } else {
+                split_flux_a(wj.r, wj.v, wj.u, wj.p, wj.sb, wj.isb, sg, ph.gm1_inv, gj);
+                split_flux_a(w0.r, w0.v, w0.u, w0.p, w0.sb, w0.isb, sg, ph.gm1_inv, g0);
+                const double w = g.wn[at];
+                R[0] += w * (gj[0] - g0[0]);
+                R[1] += w * (gj[2] - g0[2]);
+                R[2] += w * (gj[1] - g0[1]);
+                R[3] += w * (gj[3] - g0[3]);
+            }
+        }
+    }
+    if (PART == 0) {
+        Racc[t] = V4{R[0], R[1], R[2], R[3]};
+    } else {
+        V4 a = Racc[t];
+        a.a += R[0];
+        a.b += R[1];
+        a.c += R[2];
+        a.d += R[3];
+        Racc[t] = a;
+    }
+}
+
+template <int MODE, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_stage_split(const DevGeom g, const Physics ph,
+                                                       const DevState st, const V4* __restrict__ Racc,
+                                                       V4* __restrict__ q_out) {
+    const int64_t t = int64_t(blockIdx.x) * BLOCK + threadIdx.x;
+    const int64_t d = t >> g.cshift;
+    double r2 = 0.0;
+    if (d < g.n) {
+        const int8_t fl = g.flag[d];
+        const bool fixed = ph.outer_fixed && fl == LSKUM_OUTER;
+        double R[4] = {0.0, 0.0, 0.0, 0.0};
+        if (!fixed) {
+            const V4 a = Racc[t];
+            R[0] = a.a;
+            R[1] = a.b;
+            R[2] = a.c;
+            R[3] = a.d;
+            if (fl != LSKUM_INTERIOR) {
+                const double2 nn = g.nrm[d];
+                const double tx = nn.y, ty = -nn.x;
+                const double rs = R[1], rn = R[2];
+                R[1] = rs * tx + rn * nn.x;
+                R[2] = rs * ty + rn * nn.y;
+            }
+        }
+        r2 = stage_epilogue<MODE>(g, ph, st, t, d, fl, fixed, R, q_out);
+    }
+    if (MODE == 1) {
+        if (g.cshift == 0) {
+            const double s = block_sum<BLOCK>(r2);
+            if (threadIdx.x == 0) st.partials[blockIdx.x] = s;
+        } else if (d < g.n) {
             st.r2[t] = r2;
         }
     }
@@ -560,6 +726,37 @@ cudaError_t launch_flux(int mode, const DevGeom& g, const Physics& ph, const Dev
     } else {
         if (g14) flux_dispatch<kDefaultBlock, true>(mode, g, ph, st, q_in, dq, q_out, s);
         else flux_dispatch<kDefaultBlock, false>(mode, g, ph, st, q_in, dq, q_out, s);
+    }
+    return cudaGetLastError();
+}
+
+template <int BLOCK, bool G14>
+static void flux_split_dispatch(int mode, const DevGeom& g, const Physics& ph, const DevState& st,
+                                const V4* q_in, const V8* dq, V4* q_out, cudaStream_t s) {
+    const unsigned grid = grid_nc(g, BLOCK);
+    V4* Racc = st.R;  // accumulator (R is an output only of the evaluation mode)
+    k_flux_part<0, BLOCK, G14><<<grid, BLOCK, 0, s>>>(g, ph, q_in, dq, Racc);
+    k_flux_part<1, BLOCK, G14><<<grid, BLOCK, 0, s>>>(g, ph, q_in, dq, Racc);
+    k_flux_part<2, BLOCK, G14><<<grid, BLOCK, 0, s>>>(g, ph, q_in, dq, Racc);
+    k_flux_part<3, BLOCK, G14><<<grid, BLOCK, 0, s>>>(g, ph, q_in, dq, Racc);
+    switch (mode) {
+        case 0: k_stage_split<0, BLOCK><<<grid, BLOCK, 0, s>>>(g, ph, st, Racc, q_out); break;
+        case 1: k_stage_split<1, BLOCK><<<grid, BLOCK, 0, s>>>(g, ph, st, Racc, q_out); break;
+        case 2: k_stage_split<2, BLOCK><<<grid, BLOCK, 0, s>>>(g, ph, st, Racc, q_out); break;
+        case 3: k_stage_split<3, BLOCK><<<grid, BLOCK, 0, s>>>(g, ph, st, Racc, q_out); break;
+        default: k_stage_split<4, BLOCK><<<grid, BLOCK, 0, s>>>(g, ph, st, Racc, q_out); break;
+    }
+}
+
+cudaError_t launch_flux_split(int mode, const DevGeom& g, const Physics& ph, const DevState& st,
+                              const V4* q_in, const V8* dq, V4* q_out, int block, cudaStream_t s) {
+    const bool g14 = fabs(ph.gm1_inv - 2.5) < 1e-12;
+    if (block == 256) {
+        if (g14) flux_split_dispatch<256, true>(mode, g, ph, st, q_in, dq, q_out, s);
+        else flux_split_dispatch<256, false>(mode, g, ph, st, q_in, dq, q_out, s);
+    } else {
+        if (g14) flux_split_dispatch<kDefaultBlock, true>(mode, g, ph, st, q_in, dq, q_out, s);
+        else flux_split_dispatch<kDefaultBlock, false>(mode, g, ph, st, q_in, dq, q_out, s);
     }
     return cudaGetLastError();
 }

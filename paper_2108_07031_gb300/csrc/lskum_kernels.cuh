@@ -119,6 +119,10 @@ cudaError_t launch_ls_inner(const DevGeom& g, const V4* q, const V8* dq_in, V8* 
 // mode 0: evaluate R only (written to st.R); mode 1..4: SSP-RK stage.
 cudaError_t launch_flux(int mode, const DevGeom& g, const Physics& ph, const DevState& st,
                         const V4* q_in, const V8* dq, V4* q_out, int block, cudaStream_t s);
+// The paper's four split-flux kernels + a stage kernel (ablation of launch_flux;
+// 5 launches; uses st.R as the accumulator).
+cudaError_t launch_flux_split(int mode, const DevGeom& g, const Physics& ph, const DevState& st,
+                              const V4* q_in, const V8* dq, V4* q_out, int block, cudaStream_t s);
 cudaError_t launch_residue(const DevState& st, int nblocks, int64_t n, cudaStream_t s);
 // C > 1: residue per condition from st.r2 (two deterministic phases).
 cudaError_t launch_residue_cond(const DevGeom& g, const DevState& st, cudaStream_t s);

@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <algorithm>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -61,7 +62,8 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(const __nv_bfloat16* __restri
                                                    int64_t sbk, int64_t sbn, int M, int N, int K,
                                                    const float* __restrict__ bias,
                                                    float* __restrict__ Cf,
-                                                   __nv_bfloat16* __restrict__ Cb, int64_t ldc) {
+                                                   __nv_bfloat16* __restrict__ Cb, int64_t ldc,
+                                                   int kchunk) {
     __shared__ __align__(16) __nv_bfloat16 As[kTile][kKt + kSmemPad];
     __shared__ __align__(16) __nv_bfloat16 Bs[kTile][kKt + kSmemPad];
     const int m0 = blockIdx.y * kTile, n0 = blockIdx.x * kTile;
@@ -77,20 +79,25 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(const __nv_bfloat16* __restri
             for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
     const __nv_bfloat16 zero = __float2bfloat16(0.f);
     const bool a_kfast = sak == 1, b_kfast = sbk == 1;
-    for (int k0 = 0; k0 < K; k0 += kKt) {
+    // split-K: block z reduces k in [z kchunk, (z+1) kchunk) into its own
+    // slice of Cf (summed afterwards in slice order)
+    const int kbeg = blockIdx.z * kchunk;
+    const int kend = min(K, kbeg + kchunk);
+    if (EPI == kStoreF32) Cf += int64_t(blockIdx.z) * M * ldc;
+    for (int k0 = kbeg; k0 < kend; k0 += kKt) {
         // stage: 64 x 32 elements of each operand, 16 per thread; consecutive
         // threads walk the operand's contiguous dimension (coalesced loads)
         for (int e = tid; e < kTile * kKt; e += 128) {
             const int r = a_kfast ? e / kKt : e % kTile;
             const int kk = a_kfast ? e % kKt : e / kTile;
             const int gm = m0 + r, gk = k0 + kk;
-            As[r][kk] = (gm < M && gk < K) ? A[gm * sam + gk * sak] : zero;
+            As[r][kk] = (gm < M && gk < kend) ? A[gm * sam + gk * sak] : zero;
         }
         for (int e = tid; e < kTile * kKt; e += 128) {
             const int r = b_kfast ? e / kKt : e % kTile;
             const int kk = b_kfast ? e % kKt : e / kTile;
             const int gn = n0 + r, gk = k0 + kk;
-            Bs[r][kk] = (gn < N && gk < K) ? B[gk * sbk + gn * sbn] : zero;
+            Bs[r][kk] = (gn < N && gk < kend) ? B[gk * sbk + gn * sbn] : zero;
         }
         __syncthreads();
 #pragma unroll
@@ -164,6 +171,16 @@ __global__ void k_features(const float* __restrict__ raw, int64_t n, const float
     }
 #pragma unroll
     for (int k = 21; k < kIn; ++k) f[k] = 0.f;
+}
+
+// Sum of the split-K slices in slice order (deterministic).
+__global__ void k_sum_slices(const float* __restrict__ part, int slices, int64_t n,
+                             float* __restrict__ out) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float s = 0.f;
+    for (int z = 0; z < slices; ++z) s += part[int64_t(z) * n + i];
+    out[i] = s;
 }
 
 __global__ void k_to_bf16(const float* __restrict__ src, int64_t n, __nv_bfloat16* __restrict__ dst) {
@@ -281,6 +298,7 @@ struct lskum_mlp {
     float* Af[kLayers + 1] = {nullptr};
     __nv_bfloat16* Ab[kLayers + 1] = {nullptr};
     float* dA = nullptr;   // cap x 256 scratch
+    float* slices = nullptr;  // split-K partial products of the weight gradients
     float* dZ = nullptr;   // cap x 256
     __nv_bfloat16* dZb = nullptr;
     double* partial = nullptr;
@@ -313,12 +331,36 @@ cudaError_t alloc(lskum_mlp* h, T** p, int64_t count) {
 
 inline unsigned blocks(int64_t n, int b) { return unsigned((n + b - 1) / b); }
 
+constexpr int kMaxSlices = 32;
+
 template <int EPI>
 cudaError_t gemm(lskum_mlp* h, const __nv_bfloat16* A, int64_t sam, int64_t sak,
                  const __nv_bfloat16* B, int64_t sbk, int64_t sbn, int M, int N, int K,
                  const float* bias, float* Cf, __nv_bfloat16* Cb, int64_t ldc) {
-    dim3 grid(blocks(N, kTile), blocks(M, kTile));
-    k_gemm_bf16<EPI><<<grid, 128, 0, h->stream>>>(A, sam, sak, B, sbk, sbn, M, N, K, bias, Cf, Cb, ldc);
+    dim3 grid(blocks(N, kTile), blocks(M, kTile), 1);
+    k_gemm_bf16<EPI><<<grid, 128, 0, h->stream>>>(A, sam, sak, B, sbk, sbn, M, N, K, bias, Cf, Cb, ldc,
+                                                   K);
+    return cudaGetLastError();
+}
+
+// C[M x N] (ldc = N) = A B with the contraction split over enough slices to
+// give ~4 blocks per SM: for the weight gradients, whose M x N is one 256 x
+// 256 tile grid while K is the batch.
+cudaError_t gemm_splitk(lskum_mlp* h, const __nv_bfloat16* A, int64_t sam, int64_t sak,
+                        const __nv_bfloat16* B, int64_t sbk, int64_t sbn, int M, int N, int K,
+                        float* C) {
+    const int tiles = int(blocks(N, kTile) * blocks(M, kTile));
+    int slices = std::min(kMaxSlices, std::max(1, 600 / tiles));
+    int kchunk = int(blocks(K, slices)) * 1;
+    kchunk = (kchunk + kKt - 1) / kKt * kKt;
+    slices = int(blocks(K, kchunk));
+    dim3 grid(blocks(N, kTile), blocks(M, kTile), slices);
+    k_gemm_bf16<kStoreF32><<<grid, 128, 0, h->stream>>>(A, sam, sak, B, sbk, sbn, M, N, K, nullptr,
+                                                        h->slices, nullptr, N, kchunk);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t n = int64_t(M) * N;
+    k_sum_slices<<<blocks(n, 256), 256, 0, h->stream>>>(h->slices, slices, n, C);
     return cudaGetLastError();
 }
 
@@ -351,8 +393,8 @@ int backward(lskum_mlp* h, const float* T, int64_t n) {
     for (int l = kLayers - 1; l >= 0; --l) {
         const int K = layer_in(l), N = layer_out(l);
         // dW_l [N x K] = dZ^T X_l : A(m = out unit, k = sample) = dZ[s][m], B(k = sample, n = in) = X[s][n]
-        cudaError_t e = gemm<kStoreF32>(h, h->dZb, 1, N, h->Ab[l], K, 1, N, K, int(n), nullptr,
-                                        h->g + h->L.w_off[l], nullptr, K);
+        cudaError_t e = gemm_splitk(h, h->dZb, 1, N, h->Ab[l], K, 1, N, K, int(n),
+                                    h->g + h->L.w_off[l]);
         if (e != cudaSuccess) return fail(LSKUM_ERR_CUDA, std::string("dW: ") + cudaGetErrorString(e));
         MLP_CUDA((k_colsum<<<blocks(N, 32), dim3(32, 8), 0, h->stream>>>(h->dZ, int(n), N, h->g + h->L.b_off[l]),
                   cudaGetLastError()));
@@ -414,6 +456,7 @@ int lskum_mlp_create(int64_t capacity, const float* proj, lskum_mlp** out) {
         (e = alloc(h, &h->proj, 16)) != cudaSuccess || (e = alloc(h, &h->dA, capacity * kWidth)) != cudaSuccess ||
         (e = alloc(h, &h->dZ, capacity * kWidth)) != cudaSuccess ||
         (e = alloc(h, &h->dZb, capacity * kWidth)) != cudaSuccess ||
+        (e = alloc(h, &h->slices, int64_t(kMaxSlices) * kWidth * kWidth)) != cudaSuccess ||
         (e = alloc(h, &h->partial, int64_t(blocks(capacity * kOut, 256)))) != cudaSuccess ||
         (e = alloc(h, &h->loss_dev, 1)) != cudaSuccess)
         return bail(e);
