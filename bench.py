@@ -184,7 +184,7 @@ def run_ours(args, rank, world, local):
     cloud = _cloud(args.points)
     n = cloud.n
     stream = torch.cuda.Stream()
-    solver = L.Solver.from_cloud(cloud)
+    solver = L.Solver.from_cloud(cloud, flux_split=1 if args.flux_split else 0)
     solver.set_stream(stream.cuda_stream)
     solver.set_freestream(MACH, ALPHA)
     # time a developed flow: a smooth seeded perturbation of the free stream at
@@ -262,7 +262,9 @@ def run_ours(args, rank, world, local):
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "ours",
-            "config": {"workload": f"naca0012-o-cloud-{n}pts-fp64", "points": n,
+            "config": {"workload": f"naca0012-o-cloud-{n}pts-fp64"
+                                   + ("-split-flux-kernels" if args.flux_split else ""),
+                       "points": n,
                        "mach": MACH, "alpha_deg": ALPHA, "inner_iters": 2, "rk_stages": 4,
                        "cfl": 0.2, "max_neighbours": info["max_neighbours"],
                        "parallelism": f"replicas{world}",
@@ -446,6 +448,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--points", type=int, default=WORKLOAD_POINTS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--flux-split", action="store_true",
+                    help="run the headline with the split flux kernels (profiling the ablation)")
     ap.add_argument("--no-variants", dest="variants", action="store_false",
                     help="skip the mixed-precision variant line")
     args = ap.parse_args()

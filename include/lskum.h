@@ -89,6 +89,11 @@ typedef struct {
                            kernel splitting (Section 5): one kernel per split-flux derivative
                            (dGs+/ds, dGs-/ds, dGn+/dn, dGn-/dn) and one stage-update kernel;
                            an ablation, FP64 only. */
+    double weight_power; /* least-squares weights w_j = |P_j - P_i|^-weight_power in every
+                           least-squares sum (Eqs. 11, 24, 29), 0 <= weight_power <= 8;
+                           default 0: unweighted, as the paper prints them. Applied when the
+                           per-neighbour weights are formed at create, so it costs nothing
+                           per iteration. */
 } lskum_options;
 
 /* Fills *o with the defaults listed above. Returns LSKUM_ERR_INVALID_ARG if o is NULL. */

@@ -52,6 +52,10 @@
  *     the default.
  *   - Inner iterations are Jacobi sweeps started from the first-order
  *     derivatives in every stage.
+ *   - Least squares as printed (Eqs. 11, 24, 29) are unweighted. Optional
+ *     weights w_j = |P_j - P_i|^(-weight_power) multiply every term of every
+ *     least-squares sum (the weighted normal equations); weight_power = 0 is
+ *     the printed form.
  *   - dt_i = CFL min_j |P_j - P_i| / (|u_i| + a_i), once per iteration.
  *   - residue = sqrt(sum_i R_rho,i^2) / N, from the stage-1 residual.
  *   - forces: F = -sum_wall (p_i - p_inf) n_i ds_i, ds_i half the sum of the
@@ -84,7 +88,14 @@ typedef struct {
     double wall_factor; /* weight of dGn-/dn at wall points (2: mirror wall) */
     int order;          /* 2: q~ defect correction (Eq. 27-28); 1: first order (Eq. 13) */
     int outer_mode;     /* 1: outer points held at the free stream; 0: kinetic reading */
+    double weight_power; /* least-squares weight |P_j - P_i|^-weight_power; 0: unweighted */
 } orc_cloud;
+
+/* Weight of neighbour offset (dx, dy) in the least-squares sums. */
+static double ls_weight(const orc_cloud* c, double dx, double dy) {
+    if (c->weight_power == 0.0) return 1.0;
+    return pow(dx * dx + dy * dy, -0.5 * c->weight_power);
+}
 
 /* ---------------------------------------------------------------- state maps */
 
@@ -200,9 +211,10 @@ void orc_ls_sweep(const orc_cloud* c, const double* q, const double* px, const d
             int32_t j = c->nbr[e];
             double dx = c->x[j] - c->x[i];
             double dy = c->y[j] - c->y[i];
-            sxx += dx * dx;
-            sxy += dx * dy;
-            syy += dy * dy;
+            double w = ls_weight(c, dx, dy);
+            sxx += w * dx * dx;
+            sxy += w * dx * dy;
+            syy += w * dy * dy;
             for (int m = 0; m < 4; ++m) {
                 double dq;
                 if (px == NULL) {
@@ -212,8 +224,8 @@ void orc_ls_sweep(const orc_cloud* c, const double* q, const double* px, const d
                     double qt0 = q[4 * i + m] - 0.5 * (dx * px[4 * i + m] + dy * py[4 * i + m]);
                     dq = qtj - qt0;
                 }
-                sxq[m] += dx * dq;
-                syq[m] += dy * dq;
+                sxq[m] += w * dx * dq;
+                syq[m] += w * dy * dq;
             }
         }
         double det = sxx * syy - sxy * sxy;
@@ -305,13 +317,14 @@ static int residual_point(const orc_cloud* c, int64_t i, const double* q, const 
             double Gj[4], G0[4];
             orc_split_flux(Lj, dir, sign, gamma, Gj);
             orc_split_flux(L0, dir, sign, gamma, G0);
-            sss[sl] += ds * ds;
-            ssn[sl] += ds * dn;
-            snn[sl] += dn * dn;
+            double w = ls_weight(c, dx, dy);
+            sss[sl] += w * ds * ds;
+            ssn[sl] += w * ds * dn;
+            snn[sl] += w * dn * dn;
             for (int m = 0; m < 4; ++m) {
                 double dG = Gj[m] - G0[m];
-                sdg_s[sl][m] += ds * dG;
-                sdg_n[sl][m] += dn * dG;
+                sdg_s[sl][m] += w * ds * dG;
+                sdg_n[sl][m] += w * dn * dG;
             }
         }
     }

@@ -44,7 +44,7 @@ class _Cloud(C.Structure):
     _fields_ = [("n", C.c_int64), ("x", C.c_void_p), ("y", C.c_void_p), ("nx", C.c_void_p),
                 ("ny", C.c_void_p), ("flag", C.c_void_p), ("off", C.c_void_p),
                 ("nbr", C.c_void_p), ("gamma", C.c_double), ("wall_factor", C.c_double),
-                ("order", C.c_int), ("outer_mode", C.c_int)]
+                ("order", C.c_int), ("outer_mode", C.c_int), ("weight_power", C.c_double)]
 
 
 def _load():
@@ -100,7 +100,8 @@ class OracleCloud:
     """Holds contiguous copies of a cloud's arrays for the C oracle."""
 
     def __init__(self, xy, normals, flags, nbr_offsets, nbr_idx, gamma: float = GAMMA,
-                 wall_factor: float = 2.0, order: int = 2, outer_mode: int = 1):
+                 wall_factor: float = 2.0, order: int = 2, outer_mode: int = 1,
+                 weight_power: float = 0.0):
         xy = np.asarray(xy, dtype=np.float64)
         self.x = np.ascontiguousarray(xy[:, 0])
         self.y = np.ascontiguousarray(xy[:, 1])
@@ -115,13 +116,13 @@ class OracleCloud:
         self._s = _Cloud(self.n, _ptr(self.x).value, _ptr(self.y).value, _ptr(self.nx).value,
                          _ptr(self.ny).value, _ptr(self.flag).value, _ptr(self.off).value,
                          _ptr(self.nbr).value, self.gamma, float(wall_factor), int(order),
-                         int(outer_mode))
+                         int(outer_mode), float(weight_power))
 
     @classmethod
     def from_cloud(cls, cloud, gamma: float = GAMMA, wall_factor: float = 2.0, order: int = 2,
-                   outer_mode: int = 1):
+                   outer_mode: int = 1, weight_power: float = 0.0):
         return cls(cloud.xy, cloud.normals, cloud.flags, cloud.nbr_offsets, cloud.nbr_idx, gamma,
-                   wall_factor, order, outer_mode)
+                   wall_factor, order, outer_mode, weight_power)
 
     @property
     def ref(self):

@@ -257,6 +257,7 @@ int lskum_default_options(lskum_options* o) {
     o->check_every = 50;
     o->n_conditions = 1;
     o->flux_split = 0;
+    o->weight_power = 0.0;
     return LSKUM_OK;
 }
 
@@ -274,7 +275,8 @@ int lskum_create(int64_t n, const double* xy, const double* normals, const int8_
         (o.precision != LSKUM_FP64 && o.precision != LSKUM_MIXED) ||
         (o.block_size != 0 && o.block_size != 128 && o.block_size != 256) || o.check_every < 1 ||
         o.n_conditions < 1 || o.n_conditions > 256 || (o.n_conditions & (o.n_conditions - 1)) ||
-        (o.flux_split != 0 && o.flux_split != 1) || (o.flux_split && o.precision != LSKUM_FP64))
+        (o.flux_split != 0 && o.flux_split != 1) || (o.flux_split && o.precision != LSKUM_FP64) ||
+        !(o.weight_power >= 0.0 && o.weight_power <= 8.0))
         return fail(LSKUM_ERR_INVALID_ARG, "invalid option value");
 
     lskum_ctx* c = new (std::nothrow) lskum_ctx();

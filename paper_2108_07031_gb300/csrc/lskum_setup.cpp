@@ -191,7 +191,7 @@ int build_layout(int64_t n, const double* xy, const double* normals, const int8_
         }
         const Frame F = frame_of(fl, normals + 2 * i);
         const bool use[4] = {true, true, fl != LSKUM_WALL, fl != LSKUM_OUTER};  // s+, s-, n+, n-
-        double dx[LSKUM_MAX_NEIGHBOURS], dy[LSKUM_MAX_NEIGHBOURS];
+        double dx[LSKUM_MAX_NEIGHBOURS], dy[LSKUM_MAX_NEIGHBOURS], wt[LSKUM_MAX_NEIGHBOURS];
         double ds[LSKUM_MAX_NEIGHBOURS], dn[LSKUM_MAX_NEIGHBOURS];
         int sl_s[LSKUM_MAX_NEIGHBOURS], sl_n[LSKUM_MAX_NEIGHBOURS];
         double sxx = 0, sxy = 0, syy = 0;
@@ -202,20 +202,23 @@ int build_layout(int64_t n, const double* xy, const double* normals, const int8_
             const int32_t j = idx[off[i] + k];
             dx[k] = xy[2 * j] - xy[2 * i];
             dy[k] = xy[2 * j + 1] - xy[2 * i + 1];
-            const double dist = std::sqrt(dx[k] * dx[k] + dy[k] * dy[k]);
+            const double d2 = dx[k] * dx[k] + dy[k] * dy[k];
+            const double dist = std::sqrt(d2);
             dmin = std::min(dmin, dist);
-            sxx += dx[k] * dx[k];
-            sxy += dx[k] * dy[k];
-            syy += dy[k] * dy[k];
+            // least-squares weight |P_j - P_i|^-p (1 for the unweighted default)
+            wt[k] = opt.weight_power == 0.0 ? 1.0 : std::pow(d2, -0.5 * opt.weight_power);
+            sxx += wt[k] * dx[k] * dx[k];
+            sxy += wt[k] * dx[k] * dy[k];
+            syy += wt[k] * dy[k] * dy[k];
             ds[k] = dx[k] * F.tx + dy[k] * F.ty;
             dn[k] = dx[k] * F.nx + dy[k] * F.ny;
             sl_s[k] = ds[k] < 0.0 ? 0 : (ds[k] > 0.0 ? 1 : -1);
             sl_n[k] = dn[k] < 0.0 ? 2 : (dn[k] > 0.0 ? 3 : -1);
             for (int sl : {sl_s[k], sl_n[k]}) {
                 if (sl < 0 || !use[sl]) continue;
-                sss[sl] += ds[k] * ds[k];
-                ssn[sl] += ds[k] * dn[k];
-                snn[sl] += dn[k] * dn[k];
+                sss[sl] += wt[k] * ds[k] * ds[k];
+                ssn[sl] += wt[k] * ds[k] * dn[k];
+                snn[sl] += wt[k] * dn[k] * dn[k];
                 members[sl] += 1;
             }
         }
@@ -255,19 +258,19 @@ int build_layout(int64_t n, const double* xy, const double* normals, const int8_
             const int a = sl_s[k];
             if (a >= 0 && use[a]) {
                 s_code = (a == 0) ? 1u : 2u;
-                ws = (ds[k] * snn[a] - dn[k] * ssn[a]) / sdet[a];
+                ws = wt[k] * (ds[k] * snn[a] - dn[k] * ssn[a]) / sdet[a];
             }
             const int b = sl_n[k];
             if (b >= 0 && use[b]) {
                 n_code = (b == 2) ? 1u : 2u;
-                wn = (dn[k] * sss[b] - ds[k] * ssn[b]) / sdet[b];
+                wn = wt[k] * (dn[k] * sss[b] - ds[k] * ssn[b]) / sdet[b];
                 if (b == 3) wn *= wall_fac;
             }
             L.nbr[at] = uint32_t(L.user_to_dev[j]) | (s_code << kIndexBits) | (n_code << (kIndexBits + 2));
             L.hdx[at] = 0.5 * dx[k];
             L.hdy[at] = 0.5 * dy[k];
-            L.wx[at] = (dx[k] * syy - dy[k] * sxy) / det;
-            L.wy[at] = (dy[k] * sxx - dx[k] * sxy) / det;
+            L.wx[at] = wt[k] * (dx[k] * syy - dy[k] * sxy) / det;
+            L.wy[at] = wt[k] * (dy[k] * sxx - dx[k] * sxy) / det;
             L.ws[at] = ws;
             L.wn[at] = wn;
         }

@@ -52,7 +52,8 @@ class Options(C.Structure):
     _fields_ = [("gamma", C.c_double), ("cfl", C.c_double), ("inner_iters", C.c_int),
                 ("order", C.c_int), ("wall_factor", C.c_double), ("outer_mode", C.c_int),
                 ("precision", C.c_int), ("reorder", C.c_int), ("block_size", C.c_int),
-                ("check_every", C.c_int), ("n_conditions", C.c_int), ("flux_split", C.c_int)]
+                ("check_every", C.c_int), ("n_conditions", C.c_int), ("flux_split", C.c_int),
+                ("weight_power", C.c_double)]
 
 
 def library_path() -> str:

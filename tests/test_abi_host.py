@@ -50,6 +50,7 @@ def test_default_options():
     o = L.default_options()
     assert o.gamma == 1.4 and o.cfl == 0.2 and o.inner_iters == 2 and o.order == 2
     assert o.wall_factor == 2.0 and o.outer_mode == L.OUTER_FREESTREAM and o.reorder == 1
+    assert o.weight_power == 0.0 and o.flux_split == 0 and o.n_conditions == 1
 
 
 def test_error_strings():
@@ -70,7 +71,7 @@ def _create_code(c, **kw):
     off = kw.get("off", c.nbr_offsets)
     idx = kw.get("idx", c.nbr_idx)
     lib = L.load()
-    o = L.default_options()
+    o = L.default_options(**kw.get("options", {}))
     h = C.c_void_p()
     xy = np.ascontiguousarray(xy, np.float64)
     nrm = np.ascontiguousarray(nrm, np.float64)
@@ -84,6 +85,14 @@ def _create_code(c, **kw):
     else:
         assert not h.value
     return code, lib.lskum_last_error().decode()
+
+
+@pytest.mark.parametrize("bad", [dict(weight_power=-1.0), dict(weight_power=9.0),
+                                 dict(weight_power=float("nan")), dict(n_conditions=3),
+                                 dict(flux_split=1, precision=1), dict(order=3)])
+def test_create_rejects_invalid_options(bad):
+    code, msg = _create_code(_small_cloud(), options=bad)
+    assert code == -1 and "option" in msg
 
 
 def test_create_rejects_out_of_range_neighbour():

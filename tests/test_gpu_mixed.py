@@ -65,9 +65,10 @@ def test_mixed_uniform_state_zero_residual(c_ragged):
 
 
 @pytest.mark.parametrize("opts", [dict(order=1, inner_iters=0), dict(outer_mode=0),
-                                  dict(block_size=256), dict(inner_iters=3)])
+                                  dict(block_size=256), dict(inner_iters=3),
+                                  dict(weight_power=2.0)])
 def test_mixed_option_variants(c_ragged, opts):
-    ok = {k: v for k, v in opts.items() if k in ("order", "outer_mode")}
+    ok = {k: v for k, v in opts.items() if k in ("order", "outer_mode", "weight_power")}
     oc = O.OracleCloud.from_cloud(c_ragged, **ok)
     W = Cl.perturbed_state(c_ragged, 0.85, 1.0)
     R_o, _ = O.residual_of_state(oc, W, inner=opts.get("inner_iters", 2))

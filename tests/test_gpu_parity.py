@@ -153,9 +153,12 @@ def test_1000_iterations_parity(c5k):
     dict(reorder=0),
     dict(wall_factor=1.0),
     dict(flux_split=1),
+    dict(weight_power=2.0),
+    dict(weight_power=1.0, inner_iters=3),
 ])
 def test_option_variants_parity(c_ragged, opts):
-    ok = {k: v for k, v in opts.items() if k in ("order", "wall_factor", "outer_mode")}
+    ok = {k: v for k, v in opts.items()
+          if k in ("order", "wall_factor", "outer_mode", "weight_power")}
     oc = oracle_for(c_ragged, **ok)
     W = Cl.perturbed_state(c_ragged, 0.85, 1.0)
     inner = opts.get("inner_iters", 2)

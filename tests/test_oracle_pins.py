@@ -172,26 +172,50 @@ def oc5k(cloud5k):
     return O.OracleCloud.from_cloud(cloud5k)
 
 
-def test_first_order_ls_exact_for_linear_fields(cloud5k, oc5k):
-    """Eq. 11 reproduces the gradient of any linear field exactly."""
+@pytest.mark.parametrize("weight_power", [0.0, 2.0])
+def test_first_order_ls_exact_for_linear_fields(cloud5k, weight_power):
+    """Eq. 11 (plain or distance-weighted) reproduces the gradient of any
+    linear field exactly."""
+    oc = O.OracleCloud.from_cloud(cloud5k, weight_power=weight_power)
     x, y = cloud5k.xy[:, 0], cloud5k.xy[:, 1]
     a, b, c = RNG.normal(size=(3, 4))
     q = a[None, :] + b[None, :] * x[:, None] + c[None, :] * y[:, None]
-    qx, qy = O.q_derivatives(oc5k, q, 0)
+    qx, qy = O.q_derivatives(oc, q, 0)
     assert np.allclose(qx, np.broadcast_to(b, qx.shape), rtol=1e-8, atol=1e-8)
     assert np.allclose(qy, np.broadcast_to(c, qy.shape), rtol=1e-8, atol=1e-8)
 
 
-def test_first_order_ls_matches_library_lstsq(cloud5k, oc5k):
-    """Eq. 11's 2x2 normal equations equal numpy's least-squares solution."""
+def _row_scale(d, weight_power):
+    """sqrt of the least-squares weight |d|^-p of each offset row: scaling the
+    rows of a least-squares system by it gives the weighted normal equations."""
+    return np.hypot(d[:, 0], d[:, 1]) ** (-0.5 * weight_power)
+
+
+@pytest.mark.parametrize("weight_power", [0.0, 1.0, 2.0])
+def test_first_order_ls_matches_library_lstsq(cloud5k, weight_power):
+    """Eq. 11's 2x2 normal equations (optionally weighted by |P_j - P_i|^-p)
+    equal numpy's least-squares solution of the row-scaled system."""
+    oc = O.OracleCloud.from_cloud(cloud5k, weight_power=weight_power)
     q = RNG.normal(size=(cloud5k.n, 4))
-    qx, qy = O.q_derivatives(oc5k, q, 0)
+    qx, qy = O.q_derivatives(oc, q, 0)
     for i in RNG.choice(cloud5k.n, 60, replace=False):
         nb = cloud5k.neighbours(i)
         A = cloud5k.xy[nb] - cloud5k.xy[i]
-        sol, *_ = np.linalg.lstsq(A, q[nb] - q[i], rcond=None)
+        r = _row_scale(A, weight_power)[:, None]
+        sol, *_ = np.linalg.lstsq(r * A, r * (q[nb] - q[i]), rcond=None)
         assert np.allclose(sol[0], qx[i], rtol=1e-9, atol=1e-9 * np.abs(sol).max())
         assert np.allclose(sol[1], qy[i], rtol=1e-9, atol=1e-9 * np.abs(sol).max())
+
+
+def test_weights_change_the_derivative_of_a_nonlinear_field(cloud5k, oc5k):
+    """The weight option is live: for a field that is not linear the weighted
+    and unweighted fits differ (and agree again for p = 0)."""
+    q, _, _ = _quadratic(cloud5k, np.random.Generator(np.random.PCG64(8)))
+    qx0, _ = O.q_derivatives(oc5k, q, 0)
+    qx2, _ = O.q_derivatives(O.OracleCloud.from_cloud(cloud5k, weight_power=2.0), q, 0)
+    qxz, _ = O.q_derivatives(O.OracleCloud.from_cloud(cloud5k, weight_power=0.0), q, 0)
+    assert np.array_equal(qxz, qx0)
+    assert np.abs(qx2 - qx0).max() > 1e-6 * np.abs(qx0).max()
 
 
 def _quadratic(cloud, rng):
@@ -204,10 +228,14 @@ def _quadratic(cloud, rng):
     return q, qx, qy
 
 
-def test_defect_correction_is_exact_for_quadratics(cloud5k, oc5k):
+@pytest.mark.parametrize("weight_power", [0.0, 2.0])
+def test_defect_correction_is_exact_for_quadratics(cloud5k, oc5k, weight_power):
     """k-exactness for degree <= 2 (Section 2.1, after Eq. 23): fed the exact
-    derivatives of a quadratic, one sweep of Eq. 29 returns them."""
+    derivatives of a quadratic, one sweep of Eq. 29 returns them (with or
+    without least-squares weights)."""
     q, qx, qy = _quadratic(cloud5k, np.random.Generator(np.random.PCG64(5)))
+    if weight_power:
+        oc5k = O.OracleCloud.from_cloud(cloud5k, weight_power=weight_power)
     nx, ny = O.ls_sweep(oc5k, q, qx, qy)
     scale = max(np.abs(qx).max(), np.abs(qy).max())
     assert np.abs(nx - qx).max() < 1e-9 * scale
@@ -323,11 +351,12 @@ def test_kinetic_wall_is_consistent_for_mirror_symmetric_flow():
     assert errs1[2] > 0.05, errs1
 
 
-@pytest.mark.parametrize("outer_mode", [1, 0])
-def test_residual_matches_lstsq_restatement(cloud5k, outer_mode):
+@pytest.mark.parametrize("outer_mode,weight_power", [(1, 0.0), (0, 0.0), (1, 1.5)])
+def test_residual_matches_lstsq_restatement(cloud5k, outer_mode, weight_power):
     """Point residuals re-assembled with library least squares per split stencil
-    (Eq. 14 membership, Eq. 24 derivatives, frames and boundary readings)."""
-    oc = O.OracleCloud.from_cloud(cloud5k, outer_mode=outer_mode)
+    (Eq. 14 membership, Eq. 24 derivatives, frames and boundary readings;
+    weighted rows when weight_power > 0)."""
+    oc = O.OracleCloud.from_cloud(cloud5k, outer_mode=outer_mode, weight_power=weight_power)
     W = Cl.perturbed_state(cloud5k, 0.63, 2.0, amplitude=0.05)
     q = O.prim_to_q(W)
     qx, qy = O.q_derivatives(oc, q, 2)
@@ -364,7 +393,8 @@ def test_residual_matches_lstsq_restatement(cloud5k, outer_mode):
         for mask, direction, sign, comp in stencils:
             dG = O.split_flux(Lj[mask], direction, sign) - O.split_flux(L0[mask], direction, sign)
             A = np.stack([ds[mask], dn[mask]], 1)
-            sol, *_ = np.linalg.lstsq(A, dG, rcond=None)
+            r = _row_scale(d[mask], weight_power)[:, None]
+            sol, *_ = np.linalg.lstsq(r * A, r * dG, rcond=None)
             Rl += sol[comp] * (2.0 if (f == 1 and direction == 1) else 1.0)
         Rg = np.array([Rl[0], Rl[1] * t[0] + Rl[2] * nn[0], Rl[1] * t[1] + Rl[2] * nn[1], Rl[3]])
         assert np.allclose(R[i], Rg, rtol=1e-8, atol=1e-9 * np.abs(Rg).max()), (i, f, R[i], Rg)
