@@ -3,17 +3,17 @@
 1. Polynomial pieces for the split-flux erfc.
 
 The kinetic split fluxes need A = erfc(x) / 2 and B ~ exp(-x^2) at the same
-argument. The device code evaluates
-  * erf(x) = x P(x^2) for |x| <= 0.5 (then A = 1/2 - erf(x)/2), and
-  * erfc(a) = exp(-a^2) erfcx(a) for 0.5 < a <= 6, reusing exp(-a^2) from B,
-    with erfcx (the scaled complementary error function) as a polynomial in
-    (a - c_k) on 22 intervals of width 1/4 centred at c_k.
-Each polynomial is the Chebyshev interpolant of the function (computed with
-mpmath at 50 digits from the definitions erf(x) = 2/sqrt(pi) int_0^x e^-t^2 dt
-and erfcx(a) = e^(a^2) erfc(a)) converted to the monomial basis of the local
-variable; the script checks the relative error of every piece at 2000 points
-in double-precision Horner evaluation and refuses to write the header unless
-it is below 4e-16.
+argument. The device code evaluates erfc(a) = exp(-a^2) erfcx(a) for
+0 <= a = |x| <= 6, reusing exp(-a^2) from B, with erfcx (the scaled
+complementary error function, smooth and positive on the whole range) as a
+polynomial in (a - c_k) on 48 intervals of width 1/8 centred at c_k; the
+interval index is floor(8 a), which the device takes from the bits of a.
+One formula for every argument keeps the lanes of a warp on one path.
+Each polynomial is the Chebyshev interpolant of erfcx (computed with mpmath
+at 50 digits from erfcx(a) = e^(a^2) erfc(a)) converted to the monomial
+basis of the local variable; the script checks the relative error of every
+piece at 2000 points in double-precision Horner evaluation and refuses to
+write the header unless it is below 4e-16.
 
 2. The exponential by Tang's table-driven method: x = k ln2/64 + r with
 |r| <= ln2/128, exp(x) = 2^(k div 64) * 2^((k mod 64)/64) * e^r; the table
@@ -30,9 +30,8 @@ import numpy as np
 
 mp.mp.dps = 50
 
-ERF_DEG = 9           # degree of P in t = x^2 on [0, 0.25]
-CX_LO, CX_HI, CX_W = 0.5, 6.0, 0.25
-CX_DEG = 11           # degree in z = a - c on [-1/8, 1/8]
+CX_LO, CX_HI, CX_W = 0.0, 6.0, 0.125
+CX_DEG = 9            # degree in z = a - c on [-1/16, 1/16]
 
 
 def cheb_to_monomial(f, lo, hi, deg, shift):
@@ -58,19 +57,6 @@ def horner(c, z):
 
 
 def main():
-    out = []
-    # erf(x) / x = P(x^2)
-    def erf_over_x(t):
-        x = mp.sqrt(t)
-        return mp.erf(x) / x if t != 0 else 2 / mp.sqrt(mp.pi)
-    P = cheb_to_monomial(erf_over_x, mp.mpf(0), mp.mpf("0.25"), ERF_DEG, mp.mpf(0))
-    xs = np.linspace(1e-6, 0.5, 2000)
-    ref = np.array([float(mp.erf(mp.mpf(float(x)))) for x in xs])
-    got = xs * horner(P, xs * xs)
-    err = np.max(np.abs(got - ref) / np.abs(ref))
-    assert err < 4e-16, ("erf", err)
-    out.append(("kErfP", [float(c) for c in P], err))
-
     centres = []
     pieces = []
     worst = 0.0
@@ -99,15 +85,10 @@ def main():
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "math_tables.h")
     with open(path, "w") as f:
         f.write("// Generated by gen_math_tables.py -- do not edit.\n")
-        f.write("// Chebyshev interpolants (mpmath, 50 digits) of erf(x)/x in x^2 on [0, 1/4] and of\n")
-        f.write("// erfcx(a) = exp(a^2) erfc(a) in (a - c_k) on 1/4-wide intervals of [0.5, 6].\n")
-        f.write(f"// Max relative error in double Horner: erf {out[0][2]:.2e}, erfcx {worst:.2e}.\n")
+        f.write("// Chebyshev interpolants (mpmath, 50 digits) of erfcx(a) = exp(a^2) erfc(a)\n")
+        f.write(f"// in (a - c_k) on intervals of width {CX_W} covering [{CX_LO}, {CX_HI}].\n")
+        f.write(f"// Max relative error in double Horner: {worst:.2e}.\n")
         f.write("#pragma once\n\nnamespace lskum {\n\n")
-        f.write(f"constexpr int kErfDeg = {ERF_DEG};\n")
-        f.write("__device__ __constant__ const double kErfP[kErfDeg + 1] = {\n")
-        for cf in out[0][1]:
-            f.write(f"    {cf!r},\n")
-        f.write("};\n\n")
         f.write(f"constexpr double kErfcxLo = {CX_LO!r};\nconstexpr double kErfcxHi = {CX_HI!r};\n")
         f.write(f"constexpr double kErfcxInvW = {1.0 / CX_W!r};\n")
         f.write(f"constexpr int kErfcxPieces = {len(pieces)};\nconstexpr int kErfcxDeg = {CX_DEG};\n")
@@ -123,7 +104,7 @@ def main():
         for j in range(0, 64, 4):
             f.write("    " + ", ".join(repr(v) for v in tab[j:j + 4]) + ",\n")
         f.write("};\n\n}  // namespace lskum\n")
-    print(f"wrote {path}: erf err {out[0][2]:.2e}, erfcx worst {worst:.2e}, {len(pieces)} pieces")
+    print(f"wrote {path}: erfcx worst {worst:.2e}, {len(pieces)} pieces")
 
 
 if __name__ == "__main__":

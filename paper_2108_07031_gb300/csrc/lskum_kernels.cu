@@ -36,30 +36,47 @@ constexpr double kInvSqrtPi = 0.56418958354775628695;  // 1 / sqrt(pi)
 
 __device__ __forceinline__ V4 ld4(const V4* p) { return *p; }
 
+// Bit-pattern helpers: comparisons and sign flips of doubles done on the
+// integer pipe, which leaves the FP64 pipe (the flux kernel's bound) alone.
+constexpr int64_t kSignBit = int64_t(0x8000000000000000ULL);
+constexpr int64_t kAbsMask = 0x7FFFFFFFFFFFFFFFLL;
+constexpr int64_t kBits700 = 0x4085E00000000000LL;  // 700.0
+constexpr int64_t kBits6 = 0x4018000000000000LL;    // 6.0, the end of the erfcx table
+static_assert(kErfcxLo == 0.0 && kErfcxInvW == 8.0 && kErfcxHi == 6.0,
+              "erfcx_piece assumes 1/8-wide pieces on [0, 6]");
+
+__device__ __forceinline__ int64_t dbits(const double x) { return __double_as_longlong(x); }
+__device__ __forceinline__ double bitsd(const int64_t b) { return __longlong_as_double(b); }
+
+// Primitive state of one modified state q~ in the flux's frame, with the
+// per-state factors the split fluxes share: sqrt(beta), 1/sqrt(pi beta),
+// p + rho e and rho e + p/2 (|u|^2 is frame-invariant, so these are too).
 struct Prim {
-    double r, u, v, p, sb, isb;  // density, velocity (frame components), pressure, sqrt(beta), 1/sqrt(beta)
+    double r, u, v, p, sb, cb, h, k;
 };
 
-// exp(x) by Tang's table-driven method (math_tables.h): x = k ln2/64 + r,
-// |r| <= ln2/128, exp(x) = 2^(k>>6) 2^((k&63)/64) e^r with e^r - 1 from its
-// degree-6 Taylor polynomial (remainder < 3e-20): about 11 FP64 operations
-// against the library's ~18. Outside |x| <= 700 the library exp (the scaling
-// below stays in the normal range inside it).
+// exp(x) 2^-HALVE by Tang's table-driven method (math_tables.h): x = k ln2/64
+// + r, |r| <= ln2/128, exp(x) = 2^(k>>6) 2^((k&63)/64) e^r with e^r - 1 from
+// its degree-5 Taylor polynomial (remainder < 4e-17); max error 1.2 ulp
+// (checked against 400-bit arithmetic with exact FMA emulation). About 10
+// FP64 operations against the library's ~18; the power of two, including
+// the optional halving, is an integer add to the exponent field (the result
+// stays normal for |x| <= 700). Outside that range the library exp.
+template <int HALVE>
 __device__ __forceinline__ double exp_tab(const double x) {
-    if (!(fabs(x) <= 700.0)) return exp(x);
+    if ((dbits(x) & kAbsMask) > kBits700) return HALVE ? 0.5 * exp(x) : exp(x);
     const double shifter = 6755399441055744.0;  // 1.5 * 2^52: rounds k into the low bits
     double kd = fma(x, kInvLn2By64, shifter);
-    const int64_t k = __double_as_longlong(kd) - 0x4338000000000000LL;
+    const int64_t k = dbits(kd) - 0x4338000000000000LL;
     kd -= shifter;
     const double r = fma(-kd, kLn2By64Lo, fma(-kd, kLn2By64Hi, x));
-    const double p =
-        r * fma(r, fma(r, fma(r, fma(r, fma(r, 1.0 / 720.0, 1.0 / 120.0), 1.0 / 24.0), 1.0 / 6.0), 0.5), 1.0);
+    const double p = r * fma(r, fma(r, fma(r, fma(r, 1.0 / 120.0, 1.0 / 24.0), 1.0 / 6.0), 0.5), 1.0);
     const double t = kExp2Tab[k & 63];
     const double res = fma(t, p, t);
-    return __longlong_as_double(__double_as_longlong(res) + ((k >> 6) << 52));
+    return bitsd(dbits(res) + (((k >> 6) - HALVE) << 52));
 }
 
-// q -> primitive (inverse of Eq. 26); velocities in the global frame. With
+// q~ -> primitive (inverse of Eq. 26); velocities in the global frame. With
 // gamma = 1.4 (1/(gamma-1) = 5/2) the factor beta^(-1/(gamma-1)) of the
 // density is (1/sqrt(beta))^5, so no logarithm is needed; 1/sqrt(beta) is
 // needed by the split fluxes anyway.
@@ -68,66 +85,88 @@ __device__ __forceinline__ Prim q_to_prim(const double t0, const double t1, cons
                                           const double t3, const double gm1_inv) {
     Prim w;
     const double beta = -0.5 * t3;
-    w.isb = rsqrt(beta);
-    w.sb = beta * w.isb;
-    const double i2 = w.isb * w.isb;  // 1 / beta
-    const double inv2b = 0.5 * i2;    // 1 / (2 beta)
+    const double isb = rsqrt(beta);
+    w.sb = beta * isb;
+    w.cb = isb * kInvSqrtPi;
+    const double i2 = isb * isb;     // 1 / beta
+    const double inv2b = 0.5 * i2;   // 1 / (2 beta)
     w.u = t1 * inv2b;
     w.v = t2 * inv2b;
-    const double uu = w.u * w.u + w.v * w.v;
+    const double uu = fma(w.u, w.u, w.v * w.v);
     if (G14) {
-        w.r = exp_tab(t0 + beta * uu) * (i2 * i2 * w.isb);
+        w.r = exp_tab<0>(fma(beta, uu, t0)) * (i2 * i2 * isb);
     } else {
-        w.r = exp_tab(t0 - log(beta) * gm1_inv + beta * uu);
+        w.r = exp_tab<0>(t0 - log(beta) * gm1_inv + beta * uu);
     }
     w.p = w.r * inv2b;
+    const double rhoe = fma(0.5 * w.r, uu, w.p * gm1_inv);
+    w.h = w.p + rhoe;
+    w.k = fma(0.5, w.p, rhoe);
     return w;
 }
 
-// erfc(x) / 2 given e = exp(-x^2): erf(x) = x P(x^2) for |x| <= 0.5, and
-// erfc(|x|) = e erfcx(|x|) on [0.5, 6] from the piecewise polynomials of
-// math_tables.h (the exponential is shared with the split flux's B term);
-// beyond 6 the library erfc (where erfc < 2e-17).
-__device__ __forceinline__ double half_erfc(const double x, const double e) {
-    const double a = fabs(x);
-    if (a <= 0.5) {
-        const double t = x * x;
-        double pv = kErfP[kErfDeg];
-#pragma unroll
-        for (int k = kErfDeg - 1; k >= 0; --k) pv = fma(pv, t, kErfP[k]);
-        return 0.5 - 0.5 * (x * pv);
-    }
-    double ec;
-    if (a <= kErfcxHi) {
-        const int k = min(int((a - kErfcxLo) * kErfcxInvW), kErfcxPieces - 1);
-        const double* c = kErfcxC[k];
-        const double z = a - __ldg(c);
+// Index of the 1/8-wide erfcx piece holding a (0 <= a <= 6), floor(8 a),
+// from the bit pattern of a = 1.f x 2^e: 8 a = (2^52 + f) / 2^(49 - e).
+__device__ __forceinline__ int erfcx_piece(const int64_t abits) {
+    const int sh = 49 - (int(abits >> 52) - 1023);
+    const int64_t m = (abits & 0x000FFFFFFFFFFFFFLL) | 0x0010000000000000LL;
+    const int k = sh > 52 ? 0 : int(m >> sh);
+    return min(k, kErfcxPieces - 1);
+}
+
+// Kinetic split flux along the frame's first axis ("a" = ua, "b" = ub) of
+// the state w, for molecules with positive (nmask = 0) or negative (nmask =
+// sign bit) a-velocity. With S = ua sqrt(beta) and sg = +-1:
+//   A = erfc(-sg S)/2, B = exp(-S^2)/(2 sqrt(pi beta)),
+//   G = (rho (ua A + sg B), (p + rho ua^2) A + sg rho ua B, rho ub (ua A + sg B),
+//        (p + rho e) ua A + sg (rho e + p/2) B).
+// erfc(|S|)/2 = exp(-S^2)/2 erfcx(|S|) from the erfcx pieces for every |S| <= 6
+// (one path for all lanes), sharing exp(-S^2)/2 with B; the library erfc beyond.
+__device__ __forceinline__ void split_flux_a(const Prim& w, const double ua, const double ub,
+                                             const int64_t nmask, double g[4]) {
+    const double S = ua * w.sb;
+    const double eh = exp_tab<1>(-(S * S));  // exp(-S^2) / 2
+    const int64_t abits = dbits(S) & kAbsMask;
+    double hc;  // erfc(|S|) / 2
+    if (abits <= kBits6) {
+        const double* c = kErfcxC[erfcx_piece(abits)];
+        const double z = bitsd(abits) - __ldg(c);
         double pv = __ldg(c + 1 + kErfcxDeg);
 #pragma unroll
         for (int m = kErfcxDeg - 1; m >= 0; --m) pv = fma(pv, z, __ldg(c + 1 + m));
-        ec = e * pv;
+        hc = eh * pv;
     } else {
-        ec = erfc(a);
+        hc = 0.5 * erfc(bitsd(abits));
     }
-    return x > 0.0 ? 0.5 * ec : 1.0 - 0.5 * ec;
+    // A = erfc(x)/2 at x = -sg S: erfc(|x|)/2 for x > 0, 1 - erfc(|x|)/2 otherwise
+    const int64_t xbits = dbits(S) ^ nmask ^ kSignBit;
+    const double A = xbits > 0 ? hc : 1.0 - hc;
+    const double Bs = bitsd(dbits(eh * w.cb) ^ nmask);  // sg B
+    const double t = fma(ua, A, Bs);
+    g[0] = w.r * t;
+    const double ru = w.r * ua;
+    g[1] = fma(fma(ru, ua, w.p), A, ru * Bs);
+    g[2] = g[0] * ub;
+    g[3] = fma(w.h * ua, A, w.k * Bs);
 }
 
-// Kinetic split flux along the frame's first axis ("a" = u) with sign sg
-// (+1: molecules with positive a-velocity, -1: negative). Output (mass,
-// a-momentum, b-momentum, energy).
-__device__ __forceinline__ void split_flux_a(const double r, const double ua, const double ub,
-                                             const double p, const double sb, const double isb,
-                                             const double sg, const double gm1_inv, double g[4]) {
-    const double S = ua * sb;
-    const double e = exp_tab(-S * S);
-    const double A = half_erfc(-sg * S, e);
-    const double B = (0.5 * kInvSqrtPi) * e * isb;
-    const double rhoe = p * gm1_inv + 0.5 * r * (ua * ua + ub * ub);
-    const double t = ua * A + sg * B;
-    g[0] = r * t;
-    g[1] = (p + r * ua * ua) * A + sg * r * ua * B;
-    g[2] = r * ub * t;
-    g[3] = (p + rhoe) * ua * A + sg * (rhoe + 0.5 * p) * B;
+// Modified states q~_j and q~_0 of Eq. 28 for one neighbour (half offsets
+// hx, hy); returns false when they are bitwise equal: then every split-flux
+// difference is exactly 0 (free-stream preservation), and the pair is skipped.
+__device__ __forceinline__ bool modified_states(const bool second, const double hx, const double hy,
+                                                const V8& dj, const V8& di, double tj[4],
+                                                double t0[4]) {
+    if (second) {
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            tj[m] = fma(-hx, dj.x[m], fma(-hy, dj.y[m], tj[m]));
+            t0[m] = fma(-hx, di.x[m], fma(-hy, di.y[m], t0[m]));
+        }
+    }
+    int64_t diff = 0;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) diff |= dbits(tj[m]) ^ dbits(t0[m]);
+    return diff != 0;
 }
 
 __device__ __forceinline__ void cons_to_q(const V4& U, const Physics& ph, V4& q, double& rho,
@@ -220,8 +259,10 @@ __global__ void __launch_bounds__(BLOCK) k_ls_inner(const DevGeom g, const V4* _
         const double qjv[4] = {qj.a, qj.b, qj.c, qj.d};
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
-            // dq~ = q~_j - q~_0 (Eq. 28) with q~ = q - (dx q_x + dy q_y) / 2
-            const double dqt = (qjv[m] - qiv[m]) - (hx * (dj.x[m] - di.x[m]) + hy * (dj.y[m] - di.y[m]));
+            // dq~ = q~_j - q~_0 (Eq. 28) with q~ = q - (dx q_x + dy q_y) / 2, as
+            // differences of nearby values first (no cancellation), then two FMAs
+            const double dqt =
+                fma(-hx, dj.x[m] - di.x[m], fma(-hy, dj.y[m] - di.y[m], qjv[m] - qiv[m]));
             ax[m] += wx * dqt;
             ay[m] += wy * dqt;
         }
@@ -332,18 +373,11 @@ __global__ void __launch_bounds__(BLOCK) k_flux(const DevGeom g, const Physics p
                 const V4 qj = ld4(q_in + jt);
                 double tj[4] = {qj.a, qj.b, qj.c, qj.d};
                 double t0[4] = {qiv[0], qiv[1], qiv[2], qiv[3]};
-                if (second) {
-                    const double hx = g.hdx[at], hy = g.hdy[at];
-                    const V8 dj = dq[jt];
-#pragma unroll
-                    for (int m = 0; m < 4; ++m) {
-                        tj[m] = tj[m] - (hx * dj.x[m] + hy * dj.y[m]);
-                        t0[m] = t0[m] - (hx * di.x[m] + hy * di.y[m]);
-                    }
-                }
                 // equal modified states give dG = 0 exactly (free-stream preservation);
                 // the two inlined flux evaluations below need not round identically
-                if (tj[0] == t0[0] && tj[1] == t0[1] && tj[2] == t0[2] && tj[3] == t0[3]) continue;
+                if (!modified_states(second, second ? g.hdx[at] : 0.0, second ? g.hdy[at] : 0.0,
+                                     second ? dq[jt] : di, di, tj, t0))
+                    continue;
                 Prim wj = q_to_prim<G14>(tj[0], tj[1], tj[2], tj[3], ph.gm1_inv);
                 Prim w0 = q_to_prim<G14>(t0[0], t0[1], t0[2], t0[3], ph.gm1_inv);
                 if (local) {  // velocities into (s, n)
@@ -353,10 +387,10 @@ __global__ void __launch_bounds__(BLOCK) k_flux(const DevGeom g, const Physics p
                     w0.u = s0; w0.v = n0;
                 }
                 if (sc) {
-                    const double sg = sc == 1u ? 1.0 : -1.0;
+                    const int64_t nmask = sc == 1u ? 0 : kSignBit;
                     double gj[4], g0[4];
-                    split_flux_a(wj.r, wj.u, wj.v, wj.p, wj.sb, wj.isb, sg, ph.gm1_inv, gj);
-                    split_flux_a(w0.r, w0.u, w0.v, w0.p, w0.sb, w0.isb, sg, ph.gm1_inv, g0);
+                    split_flux_a(wj, wj.u, wj.v, nmask, gj);
+                    split_flux_a(w0, w0.u, w0.v, nmask, g0);
                     const double w = g.ws[at];
                     R[0] += w * (gj[0] - g0[0]);
                     R[1] += w * (gj[1] - g0[1]);
@@ -364,11 +398,11 @@ __global__ void __launch_bounds__(BLOCK) k_flux(const DevGeom g, const Physics p
                     R[3] += w * (gj[3] - g0[3]);
                 }
                 if (nc) {
-                    const double sg = nc == 1u ? 1.0 : -1.0;
+                    const int64_t nmask = nc == 1u ? 0 : kSignBit;
                     double gj[4], g0[4];
                     // along n: "a" = n-velocity, "b" = s-velocity
-                    split_flux_a(wj.r, wj.v, wj.u, wj.p, wj.sb, wj.isb, sg, ph.gm1_inv, gj);
-                    split_flux_a(w0.r, w0.v, w0.u, w0.p, w0.sb, w0.isb, sg, ph.gm1_inv, g0);
+                    split_flux_a(wj, wj.v, wj.u, nmask, gj);
+                    split_flux_a(w0, w0.v, w0.u, nmask, g0);
                     const double w = g.wn[at];
                     R[0] += w * (gj[0] - g0[0]);
                     R[1] += w * (gj[2] - g0[2]);  // s-momentum
@@ -427,7 +461,7 @@ __global__ void __launch_bounds__(BLOCK) k_flux_part(const DevGeom g, const Phys
         const double qiv[4] = {qi.a, qi.b, qi.c, qi.d};
         const bool second = ph.order == 2;
         const uint32_t want = (PART % 2 == 0) ? 1u : 2u;
-        const double sg = (PART % 2 == 0) ? 1.0 : -1.0;
+        const int64_t nmask = (PART % 2 == 0) ? 0 : kSignBit;
         const int c = g.cnt[d];
         for (int k = 0; k < c; ++k) {
             const int64_t at = int64_t(k) * g.stride + d;
@@ -439,16 +473,9 @@ __global__ void __launch_bounds__(BLOCK) k_flux_part(const DevGeom g, const Phys
             const V4 qj = ld4(q_in + jt);
             double tj[4] = {qj.a, qj.b, qj.c, qj.d};
             double t0[4] = {qiv[0], qiv[1], qiv[2], qiv[3]};
-            if (second) {
-                const double hx = g.hdx[at], hy = g.hdy[at];
-                const V8 dj = dq[jt];
-#pragma unroll
-                for (int m = 0; m < 4; ++m) {
-                    tj[m] = tj[m] - (hx * dj.x[m] + hy * dj.y[m]);
-                    t0[m] = t0[m] - (hx * di.x[m] + hy * di.y[m]);
-                }
-            }
-            if (tj[0] == t0[0] && tj[1] == t0[1] && tj[2] == t0[2] && tj[3] == t0[3]) continue;
+            if (!modified_states(second, second ? g.hdx[at] : 0.0, second ? g.hdy[at] : 0.0,
+                                 second ? dq[jt] : di, di, tj, t0))
+                continue;
             Prim wj = q_to_prim<G14>(tj[0], tj[1], tj[2], tj[3], ph.gm1_inv);
             Prim w0 = q_to_prim<G14>(t0[0], t0[1], t0[2], t0[3], ph.gm1_inv);
             if (local) {
@@ -459,16 +486,16 @@ __global__ void __launch_bounds__(BLOCK) k_flux_part(const DevGeom g, const Phys
             }
             double gj[4], g0[4];
             if (PART < 2) {
-                split_flux_a(wj.r, wj.u, wj.v, wj.p, wj.sb, wj.isb, sg, ph.gm1_inv, gj);
-                split_flux_a(w0.r, w0.u, w0.v, w0.p, w0.sb, w0.isb, sg, ph.gm1_inv, g0);
+                split_flux_a(wj, wj.u, wj.v, nmask, gj);
+                split_flux_a(w0, w0.u, w0.v, nmask, g0);
                 const double w = g.ws[at];
                 R[0] += w * (gj[0] - g0[0]);
                 R[1] += w * (gj[1] - g0[1]);
                 R[2] += w * (gj[2] - g0[2]);
                 R[3] += w * (gj[3] - g0[3]);
             } else {
-                split_flux_a(wj.r, wj.v, wj.u, wj.p, wj.sb, wj.isb, sg, ph.gm1_inv, gj);
-                split_flux_a(w0.r, w0.v, w0.u, w0.p, w0.sb, w0.isb, sg, ph.gm1_inv, g0);
+                split_flux_a(wj, wj.v, wj.u, nmask, gj);
+                split_flux_a(w0, w0.v, w0.u, nmask, g0);
                 const double w = g.wn[at];
                 R[0] += w * (gj[0] - g0[0]);
                 R[1] += w * (gj[2] - g0[2]);
