@@ -158,15 +158,17 @@ def _fp64_peak():
 
 # Per-unit figures of the FP64 flux/update kernel (k_flux), from one ncu
 # capture of a stage launch on the 600,138-point cloud (8,338,298 neighbour
-# entries): 1.342e9 DFMA, 0.279e9 DADD and 1.035e9 DMUL thread instructions
-# (predicated on) = 4.00e9 FP64 flops = 479.4 flops per neighbour entry, and
-# 438.2 MB of DRAM traffic = 730.2 bytes per point. Units of one launch:
+# entries): 1.226e9 DFMA, 0.281e9 DADD and 0.653e9 DMUL thread instructions
+# (predicated on) = 3.39e9 FP64 flops = 406.1 flops per neighbour entry, and
+# 438.6 MB of DRAM traffic = 730.8 bytes per point. Units of one launch:
 # neighbour entries (flops) and points (bytes); both scale in proportion with
 # the cloud size. With this instruction mix a saturated FP64 pipe reaches
-# (2 DFMA + DADD + DMUL) / (2 (DFMA + DADD + DMUL)) = 0.753 of the FMA peak.
-FLUX_FP64_FLOPS_PER_NEIGHBOUR = 479.4
-FLUX_DRAM_BYTES_PER_POINT = 730.2
-FLUX_FRAC_CEILING = 0.753
+# (2 DFMA + DADD + DMUL) / (2 (DFMA + DADD + DMUL)) = 0.784 of the FMA peak
+# (every FP64 instruction takes one issue slot of the pipe).
+FLUX_FP64_FLOPS_PER_NEIGHBOUR = 406.1
+FLUX_DRAM_BYTES_PER_POINT = 730.8
+FLUX_FRAC_CEILING = 0.784
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # 1.2586
 ALGORITHMIC_BYTES_PER_POINT_ITERATION = 4600.0  # minimal passes, gathers from cache
 
 
@@ -254,7 +256,9 @@ def run_ours(args, rank, world, local):
         nnz = int(cloud.nbr_offsets[-1])
         flux_launch_ms = flux_ms / max(flux_n, 1)
         achieved = FLUX_FP64_FLOPS_PER_NEIGHBOUR * nnz / (flux_launch_ms * 1e-3) / 1e12
-        peak = peaks.get("fp64_fma_tflops")
+        # ALU-bound kernel: the peak derived from unit counts and clocks,
+        # 152 SMs x 2 FP64 FMA per SM per clock x 2 flops x 2.07 GHz
+        peak = FP64_PEAK_TFLOPS
         mp, mp_kind = _peaks()
         cpu = cpu_baseline(args) if not args.no_cpu_baseline else None
         result = {
@@ -276,8 +280,10 @@ def run_ours(args, rank, world, local):
                 "unit": "TFLOP/s", "achieved": achieved, "peak": peak,
                 "frac": (achieved / peak) if peak else None,
                 "traffic": FLUX_DRAM_BYTES_PER_POINT * n,
-                "peak_source": "FP64 FMA rate measured live by pipe_peaks on this GPU "
-                               "(nominal 1.25 TFLOP/s)",
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk/SM x 2 flops x 2.07 GHz "
+                               "(maximum SM clock)",
+                "measured_fma_peak": peaks.get("fp64_fma_tflops"),
+                "measured_fma_peak_source": "pure-DFMA probe (pipe_peaks) run live on this GPU",
                 "flops_per_launch": FLUX_FP64_FLOPS_PER_NEIGHBOUR * nnz,
                 "frac_ceiling_at_instruction_mix": FLUX_FRAC_CEILING,
                 "launch_ms": flux_launch_ms,

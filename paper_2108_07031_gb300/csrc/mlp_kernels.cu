@@ -147,6 +147,187 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(const __nv_bfloat16* __restri
             }
 }
 
+// Pipelined GEMM for the aligned, large shapes: 128 x 128 tiles per block of
+// eight warps (each 64 x 32), k in stages of 32 moved global -> shared by
+// cp.async (16-byte chunks, three stages in flight), operand fragments by
+// ldmatrix -- plain for an operand whose contraction index is contiguous in
+// memory (X and W in the forward pass), transposed for one whose row index
+// is (dZ^T and X in the weight gradient, W in dZ W) -- and the same
+// mma.sync m16n8k16 and epilogues as k_gemm_bf16. Requirements (checked by
+// the caller): the contiguous dimension of each operand a multiple of 8
+// elements with 16-byte aligned rows, kchunk a multiple of 32.
+constexpr int kTB = 128;
+constexpr int kTK = 32;
+static_assert(kTK == kKt, "split-K slices hold whole k stages of both GEMM kernels");
+constexpr int kStages = 3;
+
+template <bool KFAST>
+struct TileGeo {  // shared-memory tile: [rows][ld] bf16, 16 bytes of row padding
+    static constexpr int ld = KFAST ? kTK + 8 : kTB + 8;
+    static constexpr int elems = KFAST ? kTB * ld : kTK * ld;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return uint32_t(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid) {
+    const int n = valid ? 16 : 0;  // 0: the 16 bytes are zero-filled, nothing is read
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(n));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t r[4]) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(addr));
+}
+__device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t r[4]) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(addr));
+}
+
+constexpr size_t tc_smem_bytes(bool ak, bool bk) {
+    return sizeof(__nv_bfloat16) * kStages *
+           size_t((ak ? TileGeo<true>::elems : TileGeo<false>::elems) +
+                  (bk ? TileGeo<true>::elems : TileGeo<false>::elems));
+}
+
+template <int EPI, bool AK, bool BK>
+__global__ void __launch_bounds__(256) k_gemm_bf16_tc(const __nv_bfloat16* __restrict__ A, int64_t sam,
+                                                      int64_t sak, const __nv_bfloat16* __restrict__ B,
+                                                      int64_t sbk, int64_t sbn, int M, int N, int K,
+                                                      const float* __restrict__ bias,
+                                                      float* __restrict__ Cf,
+                                                      __nv_bfloat16* __restrict__ Cb, int64_t ldc,
+                                                      int kchunk) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __nv_bfloat16* sA = reinterpret_cast<__nv_bfloat16*>(smem_raw);
+    __nv_bfloat16* sB = sA + kStages * TileGeo<AK>::elems;
+    const int m0 = blockIdx.y * kTB, n0 = blockIdx.x * kTB;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = (warp >> 2) * 64, wn = (warp & 3) * 32;
+    const int kbeg = blockIdx.z * kchunk;
+    const int kend = min(K, kbeg + kchunk);
+    const int ktiles = kend > kbeg ? (kend - kbeg + kTK - 1) / kTK : 0;
+    if (EPI == kStoreF32) Cf += int64_t(blockIdx.z) * M * ldc;
+
+    // one stage: 512 16-byte chunks of each operand tile, two per thread
+    auto load_stage = [&](int stage, int kt) {
+        const int k0 = kbeg + kt * kTK;
+        __nv_bfloat16* a = sA + stage * TileGeo<AK>::elems;
+        __nv_bfloat16* b = sB + stage * TileGeo<BK>::elems;
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int c = tid + i * 256;
+            if (AK) {
+                const int r = c >> 2, kc = (c & 3) * 8, gm = m0 + r, gk = k0 + kc;
+                const bool ok = gm < M && gk < kend;
+                cp_async16(smem_u32(a + r * TileGeo<AK>::ld + kc), ok ? A + int64_t(gm) * sam + gk : A, ok);
+            } else {
+                const int r = c >> 4, mc = (c & 15) * 8, gk = k0 + r, gm = m0 + mc;
+                const bool ok = gk < kend && gm < M;
+                cp_async16(smem_u32(a + r * TileGeo<AK>::ld + mc), ok ? A + int64_t(gk) * sak + gm : A, ok);
+            }
+            if (BK) {
+                const int r = c >> 2, kc = (c & 3) * 8, gn = n0 + r, gk = k0 + kc;
+                const bool ok = gn < N && gk < kend;
+                cp_async16(smem_u32(b + r * TileGeo<BK>::ld + kc), ok ? B + int64_t(gn) * sbn + gk : B, ok);
+            } else {
+                const int r = c >> 4, nc = (c & 15) * 8, gk = k0 + r, gn = n0 + nc;
+                const bool ok = gk < kend && gn < N;
+                cp_async16(smem_u32(b + r * TileGeo<BK>::ld + nc), ok ? B + int64_t(gk) * sbk + gn : B, ok);
+            }
+        }
+    };
+
+    float acc[4][4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
+
+#pragma unroll
+    for (int st = 0; st < kStages - 1; ++st) {
+        if (st < ktiles) load_stage(st, st);
+        cp_async_commit();
+    }
+    for (int kt = 0; kt < ktiles; ++kt) {
+        cp_async_wait<kStages - 2>();  // stage kt has landed (this thread's copies)
+        __syncthreads();                // ... everyone's; stage kt-1 is no longer read
+        const int nxt = kt + kStages - 1;
+        if (nxt < ktiles) load_stage(nxt % kStages, nxt);
+        cp_async_commit();
+        const __nv_bfloat16* a = sA + (kt % kStages) * TileGeo<AK>::elems;
+        const __nv_bfloat16* b = sB + (kt % kStages) * TileGeo<BK>::elems;
+#pragma unroll
+        for (int ks = 0; ks < kTK; ks += 16) {
+            uint32_t af[4][4], bfr[4][2];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                if (AK) {  // [m][k]: matrices (m 0-7 | 8-15) x (k 0-7 | 8-15)
+                    const int row = wm + i * 16 + (lane & 15), col = ks + (lane >> 4) * 8;
+                    ldsm_x4(smem_u32(a + row * TileGeo<AK>::ld + col), af[i]);
+                } else {   // [k][m], transposed on load
+                    const int row = ks + (lane & 7) + (lane >> 4) * 8;
+                    const int col = wm + i * 16 + ((lane >> 3) & 1) * 8;
+                    ldsm_x4_t(smem_u32(a + row * TileGeo<AK>::ld + col), af[i]);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 4; j += 2) {  // two n8 fragments per ldmatrix
+                uint32_t r[4];
+                if (BK) {  // [n][k]
+                    const int row = wn + j * 8 + (lane & 7) + (lane >> 4) * 8;
+                    const int col = ks + ((lane >> 3) & 1) * 8;
+                    ldsm_x4(smem_u32(b + row * TileGeo<BK>::ld + col), r);
+                } else {   // [k][n], transposed on load
+                    const int row = ks + (lane & 7) + ((lane >> 3) & 1) * 8;
+                    const int col = wn + j * 8 + (lane >> 4) * 8;
+                    ldsm_x4_t(smem_u32(b + row * TileGeo<BK>::ld + col), r);
+                }
+                bfr[j][0] = r[0];
+                bfr[j][1] = r[1];
+                bfr[j + 1][0] = r[2];
+                bfr[j + 1][1] = r[3];
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) mma_bf16_16816(acc[i][j], af[i], bfr[j]);
+        }
+    }
+    cp_async_wait<0>();
+
+    const int grp = lane >> 2, tig = lane & 3;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int m = m0 + wm + i * 16 + grp + ((r & 2) ? 8 : 0);
+                const int n = n0 + wn + j * 8 + tig * 2 + (r & 1);
+                if (m >= M || n >= N) continue;
+                float v = acc[i][j][r];
+                if (EPI != kStoreF32) v += bias[n];
+                if (EPI == kBiasTanh) {
+                    const float t = tanhf(v);
+                    Cf[int64_t(m) * ldc + n] = t;
+                    Cb[int64_t(m) * ldc + n] = __float2bfloat16(t);
+                } else {
+                    Cf[int64_t(m) * ldc + n] = v;
+                }
+            }
+}
+
 // Features: per sample raw (x, y, wall distance, M, alpha_deg) ->
 // [x/10, y/10, log(d + 1e-3)/5, (M - 0.55)/0.25, (alpha - 1)/5,
 //  sin(P (x, y)), cos(P (x, y)) (8 projections each), 0 x 11 padding],
@@ -333,10 +514,51 @@ inline unsigned blocks(int64_t n, int b) { return unsigned((n + b - 1) / b); }
 
 constexpr int kMaxSlices = 32;
 
+// The pipelined kernel's layout requirements (see k_gemm_bf16_tc); small
+// outputs (the 4-wide output layer, the 32-wide input layer's weight
+// gradient) stay on the 64 x 64 kernel.
+bool tc_ok(const void* A, int64_t sam, int64_t sak, const void* B, int64_t sbk, int64_t sbn, int M,
+           int N, int K) {
+    if (M < 64 || N < 64) return false;
+    const bool ak = sak == 1, bk = sbk == 1;
+    if ((!ak && sam != 1) || (!bk && sbn != 1)) return false;
+    if ((reinterpret_cast<uintptr_t>(A) & 15) || (reinterpret_cast<uintptr_t>(B) & 15)) return false;
+    if (ak ? (sam % 8 || K % 8) : (sak % 8 || M % 8)) return false;
+    if (bk ? (sbn % 8 || K % 8) : (sbk % 8 || N % 8)) return false;
+    return true;
+}
+
+template <int EPI, bool AK, bool BK>
+cudaError_t launch_tc(lskum_mlp* h, dim3 grid, const __nv_bfloat16* A, int64_t sam, int64_t sak,
+                      const __nv_bfloat16* B, int64_t sbk, int64_t sbn, int M, int N, int K,
+                      const float* bias, float* Cf, __nv_bfloat16* Cb, int64_t ldc, int kchunk) {
+    constexpr size_t smem = tc_smem_bytes(AK, BK);
+    static bool attr_set = false;  // the opt-in above 48 KB of dynamic shared memory, once
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_gemm_bf16_tc<EPI, AK, BK>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    k_gemm_bf16_tc<EPI, AK, BK><<<grid, 256, smem, h->stream>>>(A, sam, sak, B, sbk, sbn, M, N, K, bias,
+                                                                Cf, Cb, ldc, kchunk);
+    return cudaGetLastError();
+}
+
 template <int EPI>
 cudaError_t gemm(lskum_mlp* h, const __nv_bfloat16* A, int64_t sam, int64_t sak,
                  const __nv_bfloat16* B, int64_t sbk, int64_t sbn, int M, int N, int K,
                  const float* bias, float* Cf, __nv_bfloat16* Cb, int64_t ldc) {
+    if (tc_ok(A, sam, sak, B, sbk, sbn, M, N, K)) {
+        const dim3 grid(blocks(N, kTB), blocks(M, kTB), 1);
+        const int kchunk = int(blocks(K, kTK)) * kTK;
+        if (sak == 1 && sbk == 1)  // forward X W^T
+            return launch_tc<EPI, true, true>(h, grid, A, sam, sak, B, sbk, sbn, M, N, K, bias, Cf, Cb,
+                                              ldc, kchunk);
+        if (EPI == kStoreF32 && sak == 1)  // backward dZ W
+            return launch_tc<kStoreF32, true, false>(h, grid, A, sam, sak, B, sbk, sbn, M, N, K,
+                                                     nullptr, Cf, nullptr, ldc, kchunk);
+    }
     dim3 grid(blocks(N, kTile), blocks(M, kTile), 1);
     k_gemm_bf16<EPI><<<grid, 128, 0, h->stream>>>(A, sam, sak, B, sbk, sbn, M, N, K, bias, Cf, Cb, ldc,
                                                    K);
@@ -349,15 +571,24 @@ cudaError_t gemm(lskum_mlp* h, const __nv_bfloat16* A, int64_t sam, int64_t sak,
 cudaError_t gemm_splitk(lskum_mlp* h, const __nv_bfloat16* A, int64_t sam, int64_t sak,
                         const __nv_bfloat16* B, int64_t sbk, int64_t sbn, int M, int N, int K,
                         float* C) {
-    const int tiles = int(blocks(N, kTile) * blocks(M, kTile));
-    int slices = std::min(kMaxSlices, std::max(1, 600 / tiles));
-    int kchunk = int(blocks(K, slices)) * 1;
-    kchunk = (kchunk + kKt - 1) / kKt * kKt;
+    const bool tc = tc_ok(A, sam, sak, B, sbk, sbn, M, N, K) && sam == 1 && sbn == 1;
+    const int tile = tc ? kTB : kTile;
+    const int tiles = int(blocks(N, tile) * blocks(M, tile));
+    int slices = std::min(kMaxSlices, std::max(1, (tc ? 300 : 600) / tiles));
+    int kchunk = int(blocks(K, slices));
+    kchunk = (kchunk + kKt - 1) / kKt * kKt;  // kKt == kTK: whole k stages per slice
     slices = int(blocks(K, kchunk));
-    dim3 grid(blocks(N, kTile), blocks(M, kTile), slices);
-    k_gemm_bf16<kStoreF32><<<grid, 128, 0, h->stream>>>(A, sam, sak, B, sbk, sbn, M, N, K, nullptr,
-                                                        h->slices, nullptr, N, kchunk);
-    cudaError_t e = cudaGetLastError();
+    dim3 grid(blocks(N, tile), blocks(M, tile), slices);
+    cudaError_t e;
+    if (tc) {
+        // weight gradient dZ^T X: both operands transposed on load
+        e = launch_tc<kStoreF32, false, false>(h, grid, A, sam, sak, B, sbk, sbn, M, N, K, nullptr,
+                                               h->slices, nullptr, N, kchunk);
+    } else {
+        k_gemm_bf16<kStoreF32><<<grid, 128, 0, h->stream>>>(A, sam, sak, B, sbk, sbn, M, N, K, nullptr,
+                                                            h->slices, nullptr, N, kchunk);
+        e = cudaGetLastError();
+    }
     if (e != cudaSuccess) return e;
     const int64_t n = int64_t(M) * N;
     k_sum_slices<<<blocks(n, 256), 256, 0, h->stream>>>(h->slices, slices, n, C);

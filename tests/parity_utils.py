@@ -14,6 +14,13 @@ def normwise(a, b):
     return float((np.abs(a - b).max(axis=0) / scale).max())
 
 
+def linf_rel(a, b):
+    """||a - b||_inf / ||b||_inf over all entries: the one-step parity measure."""
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
 def residual_conditioning_bound(oc, W, inner=2, factor=8.0, floor=1e-12, seed=11):
     """Tolerance for an FP64 residual comparison from the problem's conditioning.
 

@@ -43,12 +43,15 @@ def _batch(n, seed):
     return feat, T
 
 
-def test_forward_and_gradients_match_reference(net):
+@pytest.mark.parametrize("n", [1000, 333, 40])
+def test_forward_and_gradients_match_reference(net, n):
     """GPU (BF16 operands, FP32 accumulation) against the FP64 reference with
     the same BF16 rounding points: outputs to 5e-3 and gradients to 2e-2
     norm-wise (activations rounded to BF16 can land on the other side of a
-    rounding boundary than in FP64)."""
-    feat, T = _batch(1000, 2)
+    rounding boundary than in FP64). Batch sizes: ragged against the 128-row
+    tiles of the pipelined GEMM (1000, 333) and below its 64-row minimum (40,
+    the 64 x 64 kernel)."""
+    feat, T = _batch(n, 2)
     p = S.init_params(3)
     p[-4:] = [0.1, -0.2, 0.05, 0.3]  # non-zero output bias
     net.set_params(p)
