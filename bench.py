@@ -51,6 +51,24 @@ def _dist():
     return rank, world, local
 
 
+def max_over_ranks(x: float, dist) -> float:
+    """Maximum of a per-rank float over all ranks (the job's wall time is its
+    slowest rank's); the identity without a process group."""
+    if dist is None:
+        return float(x)
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Units processed by all ranks (each rank does the same work: weak
+    scaling, replicas) per second of the slowest rank."""
+    return world * units_per_rank / seconds
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -223,12 +241,8 @@ def run_ours(args, rank, world, local):
                                                        ("residue", L.KERNEL_REDUCE))}
     solver.profile(False)
     clocks = clk.summary()
-    t_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = world * n * args.steps / (t_max * 1e-3)
+    t_max = max_over_ranks(ms, dist)
+    value = whole_job_rate(n * args.steps, world, t_max * 1e-3)
 
     # end to end through the C ABI with host buffers: H2D of the state,
     # one iteration, D2H of the residue, every step
@@ -243,12 +257,8 @@ def run_ours(args, rank, world, local):
         _ = solver.residual_norm()
     barrier()
     e2e_s = time.perf_counter() - t0
-    e2e_t = e2e_s
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_t = float(t.item())
-    e2e_value = world * n * e2e_steps / e2e_t
+    e2e_t = max_over_ranks(e2e_s, dist)
+    e2e_value = whole_job_rate(n * e2e_steps, world, e2e_t)
 
     result = None
     if rank == 0:
@@ -379,14 +389,9 @@ def time_variant(args, cloud, precision, n_cond, stream, barrier, dist, what,
                                                   ("residue", L.KERNEL_REDUCE))}
     s.profile(False)
     s.close()
-    t_max = ms
-    world = 1
-    if dist is not None:
-        world = dist.get_world_size()
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = world * cloud.n * n_cond * args.steps / (t_max * 1e-3)
+    world = dist.get_world_size() if dist is not None else 1
+    t_max = max_over_ranks(ms, dist)
+    value = whole_job_rate(cloud.n * n_cond * args.steps, world, t_max * 1e-3)
     return {"workload": what, "precision": "mixed" if precision == L.MIXED else "fp64",
             "points": cloud.n, "conditions": n_cond, "block_size": {"flux": block[0], "q_derivatives": block[1]},
             "value": value, "unit": "point-condition-iterations/s" if n_cond > 1 else UNIT,
