@@ -38,7 +38,7 @@ def _rank_main(rank, world, port, out):
 def test_two_gloo_ranks_take_the_slowest_rank_and_sum_the_units():
     world = 2
     port = _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.start_processes(_rank_main, args=(world, port, out), nprocs=world, join=True,
                            start_method="spawn")
