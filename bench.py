@@ -176,16 +176,16 @@ def _fp64_peak():
 
 # Per-unit figures of the FP64 flux/update kernel (k_flux), from one ncu
 # capture of a stage launch on the 600,138-point cloud (8,338,298 neighbour
-# entries): 1.226e9 DFMA, 0.281e9 DADD and 0.653e9 DMUL thread instructions
-# (predicated on) = 3.39e9 FP64 flops = 406.1 flops per neighbour entry, and
-# 438.6 MB of DRAM traffic = 730.8 bytes per point. Units of one launch:
+# entries): 1.309e9 DFMA, 0.298e9 DADD and 0.620e9 DMUL thread instructions
+# (predicated on) = 3.54e9 FP64 flops = 424.1 flops per neighbour entry, and
+# 438.2 MB of DRAM traffic = 730.1 bytes per point. Units of one launch:
 # neighbour entries (flops) and points (bytes); both scale in proportion with
 # the cloud size. With this instruction mix a saturated FP64 pipe reaches
-# (2 DFMA + DADD + DMUL) / (2 (DFMA + DADD + DMUL)) = 0.784 of the FMA peak
+# (2 DFMA + DADD + DMUL) / (2 (DFMA + DADD + DMUL)) = 0.794 of the FMA peak
 # (every FP64 instruction takes one issue slot of the pipe).
-FLUX_FP64_FLOPS_PER_NEIGHBOUR = 406.1
-FLUX_DRAM_BYTES_PER_POINT = 730.8
-FLUX_FRAC_CEILING = 0.784
+FLUX_FP64_FLOPS_PER_NEIGHBOUR = 424.1
+FLUX_DRAM_BYTES_PER_POINT = 730.1
+FLUX_FRAC_CEILING = 0.794
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # 1.2586
 ALGORITHMIC_BYTES_PER_POINT_ITERATION = 4600.0  # minimal passes, gathers from cache
 

@@ -346,13 +346,15 @@ int lskum_create(int64_t n, const double* xy, const double* normals, const int8_
             (e = upload(c, &g.wn, L.wn)) != cudaSuccess)
             return bail(e, "upload of the FP64 cloud layout");
     } else {
-        auto to32 = [](const std::vector<double>& v) { return std::vector<float>(v.begin(), v.end()); };
-        if ((e = upload(c, &c->g32.hdx, to32(L.hdx))) != cudaSuccess ||
-            (e = upload(c, &c->g32.hdy, to32(L.hdy))) != cudaSuccess ||
-            (e = upload(c, &c->g32.wx, to32(L.wx))) != cudaSuccess ||
-            (e = upload(c, &c->g32.wy, to32(L.wy))) != cudaSuccess ||
-            (e = upload(c, &c->g32.ws, to32(L.ws))) != cudaSuccess ||
-            (e = upload(c, &c->g32.wn, to32(L.wn))) != cudaSuccess)
+        // FP32 records per neighbour entry: {wx, wy, hdx, hdy} and {ws, wn, hdx, hdy}
+        std::vector<float4> lsw(L.wx.size()), fxw(L.wx.size());
+        for (size_t i = 0; i < lsw.size(); ++i) {
+            const float hx = float(L.hdx[i]), hy = float(L.hdy[i]);
+            lsw[i] = make_float4(float(L.wx[i]), float(L.wy[i]), hx, hy);
+            fxw[i] = make_float4(float(L.ws[i]), float(L.wn[i]), hx, hy);
+        }
+        if ((e = upload(c, &c->g32.lsw, lsw)) != cudaSuccess ||
+            (e = upload(c, &c->g32.fxw, fxw)) != cudaSuccess)
             return bail(e, "upload of the FP32 cloud layout");
     }
 

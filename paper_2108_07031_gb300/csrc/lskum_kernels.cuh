@@ -33,12 +33,10 @@ struct __align__(32) D8f {
 
 // FP32 copies of the slot-major per-neighbour arrays (mixed precision).
 struct DevGeom32 {
-    const float* hdx;
-    const float* hdy;
-    const float* wx;
-    const float* wy;
-    const float* ws;
-    const float* wn;
+    // slot-major [slot][stride], one 16-byte record per neighbour entry so a
+    // kernel fetches its per-neighbour constants with one vector load
+    const float4* lsw;  // {wx, wy, hdx, hdy}: least-squares weights (Eq. 11), half offsets
+    const float4* fxw;  // {ws, wn, hdx, hdy}: split-stencil weights (Eq. 24), half offsets
 };
 
 // Static cloud data on the device (device point order).

@@ -56,7 +56,8 @@ __global__ void __launch_bounds__(BLOCK) k_ls_first_mx(const DevGeom g, const De
     for (int k = 0; k < c; ++k) {
         const int64_t at = int64_t(k) * g.stride + d;
         const uint32_t j = g.nbr[at] & kIndexMask;
-        const float wx = g32.wx[at], wy = g32.wy[at];
+        const float4 lw = g32.lsw[at];
+        const float wx = lw.x, wy = lw.y;
         const float4 dqv = qdiff(q[sidx(g, j, cc)], qi);
         ax.x += wx * dqv.x; ax.y += wx * dqv.y; ax.z += wx * dqv.z; ax.w += wx * dqv.w;
         ay.x += wy * dqv.x; ay.y += wy * dqv.y; ay.z += wy * dqv.z; ay.w += wy * dqv.w;
@@ -80,8 +81,8 @@ __global__ void __launch_bounds__(BLOCK) k_ls_inner_mx(const DevGeom g, const De
     for (int k = 0; k < c; ++k) {
         const int64_t at = int64_t(k) * g.stride + d;
         const uint32_t j = g.nbr[at] & kIndexMask;
-        const float wx = g32.wx[at], wy = g32.wy[at];
-        const float hx = g32.hdx[at], hy = g32.hdy[at];
+        const float4 lw = g32.lsw[at];
+        const float wx = lw.x, wy = lw.y, hx = lw.z, hy = lw.w;
         const int64_t jt = sidx(g, j, cc);
         const float4 dqv = qdiff(q[jt], qi);
         const D8f dj = din[jt];
@@ -313,10 +314,11 @@ __global__ void __launch_bounds__(BLOCK) k_flux_mx(const DevGeom g, const DevGeo
                 const uint32_t sc = (e >> kIndexBits) & 3u;
                 const uint32_t nc = (e >> (kIndexBits + 2)) & 3u;
                 const int64_t jt = sidx(g, j, cc);
+                const float4 fw = g32.fxw[at];
                 const float4 dqv = qdiff(q_in[jt], qi);
                 float4 base = qiv, dlt = dqv;
                 if (second) {
-                    const float hx = g32.hdx[at], hy = g32.hdy[at];
+                    const float hx = fw.z, hy = fw.w;
                     const D8f dj = dq[jt];
                     // q~_0 = q_i - (dx q_x,i + dy q_y,i)/2; dq~ = q~_j - q~_0 (Eq. 28)
                     base.x = qiv.x - (hx * di.x.x + hy * di.y.x);
@@ -340,7 +342,7 @@ __global__ void __launch_bounds__(BLOCK) k_flux_mx(const DevGeom g, const DevGeo
                     float dG[4];
                     dsplit_flux_a(w.r, w.u, w.v, w.p, w.sb, w.dr, w.du, w.dv, w.dp, w.dsb, sg,
                                   gm1_inv, dG);
-                    const float wt = g32.ws[at];
+                    const float wt = fw.x;
                     R[0] += wt * dG[0]; R[1] += wt * dG[1]; R[2] += wt * dG[2]; R[3] += wt * dG[3];
                 }
                 if (nc) {
@@ -348,7 +350,7 @@ __global__ void __launch_bounds__(BLOCK) k_flux_mx(const DevGeom g, const DevGeo
                     float dG[4];
                     dsplit_flux_a(w.r, w.v, w.u, w.p, w.sb, w.dr, w.dv, w.du, w.dp, w.dsb, sg,
                                   gm1_inv, dG);
-                    const float wt = g32.wn[at];
+                    const float wt = fw.y;
                     R[0] += wt * dG[0]; R[1] += wt * dG[2]; R[2] += wt * dG[1]; R[3] += wt * dG[3];
                 }
             }
