@@ -7,7 +7,7 @@ state accumulation, q-variables, determinants, residue and forces. Its error
 is FP32 rounding relative to the residual itself (2^-24 ~ 6e-8 per
 operation, a few hundred operations per neighbour through sums of ~14 terms):
 the bound used here is 2e-5 norm-wise on one residual evaluation, and the
-BASELINE target 1e-4 on Cl/Cd after 1000 iterations.
+target 1e-4 on Cl/Cd after 1000 iterations.
 """
 
 import numpy as np
