@@ -51,6 +51,20 @@ def _dist():
     return rank, world, local
 
 
+def workload_config(points_requested: int, world: int, flux_split: bool = False) -> dict:
+    """The `config` both arms report: the NACA 0012 cloud of about
+    `points_requested` points (its exact size from the generator's grid)."""
+    from paper_2108_07031_gb300 import cloud as Cl
+    n_c, n_r = Cl.cloud_dims(points_requested)
+    n = n_c * n_r
+    return {"workload": f"naca0012-o-cloud-{n}pts-fp64" + ("-split-flux-kernels" if flux_split else ""),
+            "points": n, "mach": MACH, "alpha_deg": ALPHA, "inner_iters": 2, "rk_stages": 4,
+            "cfl": 0.2, "parallelism": f"replicas{world}",
+            "l2": "inputs larger than L2 (device working set ~12 GB), no flush",
+            "initial_state": "developed: seeded smooth perturbation of the free stream at every "
+                             "point"}
+
+
 def max_over_ranks(x: float, dist) -> float:
     """Maximum of a per-rank float over all ranks (the job's wall time is its
     slowest rank's); the identity without a process group."""
@@ -261,6 +275,8 @@ def run_ours(args, rank, world, local):
     e2e_value = whole_job_rate(n * e2e_steps, world, e2e_t)
 
     result = None
+    config = workload_config(args.points, world, args.flux_split)
+    assert config["points"] == n
     if rank == 0:
         peaks = _fp64_peak()
         nnz = int(cloud.nbr_offsets[-1])
@@ -276,15 +292,8 @@ def run_ours(args, rank, world, local):
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "ours",
-            "config": {"workload": f"naca0012-o-cloud-{n}pts-fp64"
-                                   + ("-split-flux-kernels" if args.flux_split else ""),
-                       "points": n,
-                       "mach": MACH, "alpha_deg": ALPHA, "inner_iters": 2, "rk_stages": 4,
-                       "cfl": 0.2, "max_neighbours": info["max_neighbours"],
-                       "parallelism": f"replicas{world}",
-                       "l2": "inputs larger than L2 (device working set ~12 GB), no flush",
-                       "initial_state": "developed: seeded smooth perturbation of the free "
-                                        "stream at every point"},
+            "config": config,
+            "max_neighbours": info["max_neighbours"],
             "roofline": {
                 "kernel": "k_flux (flux residual + SSP-RK stage update, FP64)", "bound": "alu",
                 "unit": "TFLOP/s", "achieved": achieved, "peak": peak,
@@ -402,9 +411,10 @@ def time_variant(args, cloud, precision, n_cond, stream, barrier, dist, what,
 def _oracle_sample_rate(iters: int):
     """Oracle pt-it/s on the 2.5M-point cloud of the same family (one iteration = one step)."""
     from oracle import oracle as O
+    from paper_2108_07031_gb300 import cloud as Cl
     cloud = _cloud(SAMPLE_POINTS)
     oc = O.OracleCloud.from_cloud(cloud)
-    W = np.tile(O.freestream(MACH, ALPHA), (cloud.n, 1))
+    W = Cl.perturbed_state(cloud, MACH, ALPHA)
     t0 = time.perf_counter()
     W, res, st = O.iterate(oc, W, iters)
     dt = time.perf_counter() - t0
@@ -424,7 +434,8 @@ def run_reference(args, rank, world):
     from oracle import oracle as O
     cloud = _cloud(SAMPLE_POINTS)
     oc = O.OracleCloud.from_cloud(cloud)
-    W = np.tile(O.freestream(MACH, ALPHA), (cloud.n, 1))
+    from paper_2108_07031_gb300 import cloud as Cl
+    W = Cl.perturbed_state(cloud, MACH, ALPHA)  # the same kind of state the GPU arm times
     for _ in range(args.warmup):
         W, _, _ = O.iterate(oc, W, 1)
     times = []
@@ -435,16 +446,15 @@ def run_reference(args, rank, world):
     total = sum(times)
     value = cloud.n * args.steps / total
     cores = O.num_threads()
-    sample = (f"1 oracle iteration per step on the {cloud.n}-point cloud of the same NACA 0012 "
-              f"family (the 10M workload's distribution at 1/4 the points)")
+    sample = (f"1 oracle iteration per step, on {cores} host cores, on the {cloud.n}-point cloud "
+              f"of the same NACA 0012 family (the workload's distribution at 1/4 of its 10M "
+              f"points), from the same kind of developed state")
     return {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "impl": "reference",
-        "config": {"workload": "naca0012-o-cloud-10003344pts-fp64", "points": WORKLOAD_POINTS,
-                   "mach": MACH, "alpha_deg": ALPHA, "inner_iters": 2, "rk_stages": 4,
-                   "cfl": 0.2, "parallelism": "host cores"},
+        "config": workload_config(args.points, world),
         "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": cores,
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},

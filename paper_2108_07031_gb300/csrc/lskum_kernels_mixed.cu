@@ -102,7 +102,12 @@ __global__ void __launch_bounds__(BLOCK) k_ls_inner_mx(const DevGeom g, const De
 struct PrimPair {
     float r, u, v, p, sb;       // base state (of q~_0): density, velocity, pressure, sqrt(beta)
     float dr, du, dv, dp, dsb;  // difference state(q~_j) - state(q~_0)
+    float isb, isbj;            // 1/sqrt(beta) of the base and of state j
 };
+
+// The FP32 quotients below are fast (reciprocal approximation times the
+// numerator, ~2 ulp): every one scales a difference term, whose own FP32
+// rounding error is larger.
 
 // From the base q~_0 and the difference dq~ = q~_j - q~_0 (inverse of Eq. 26).
 template <bool G14>
@@ -111,33 +116,35 @@ __device__ __forceinline__ PrimPair prim_pair(const float4 b, const float4 dq, c
     const float beta = -0.5f * b.w;
     const float dbeta = -0.5f * dq.w;
     const float qj4 = b.w + dq.w;
-    const float inv2b = -1.0f / b.w;  // 1 / (2 beta)
+    const float inv2b = __fdividef(-1.0f, b.w);  // 1 / (2 beta)
     w.u = b.y * inv2b;
     w.v = b.z * inv2b;
     // u = -q2/q4:  u_j - u_0 = (q2 dq4 - dq2 q4) / (q4 q4_j)
-    const float rq = 1.0f / (b.w * qj4);
+    const float rq = __fdividef(1.0f, b.w * qj4);
     w.du = (b.y * dq.w - dq.y * b.w) * rq;
     w.dv = (b.z * dq.w - dq.z * b.w) * rq;
     const float uj = w.u + w.du, vj = w.v + w.dv;
     const float uu0 = w.u * w.u + w.v * w.v;
     const float uuj = uj * uj + vj * vj;
     const float duu = w.du * (uj + w.u) + w.dv * (vj + w.v);
-    const float isb = rsqrtf(beta);
-    w.sb = beta * isb;
+    w.isb = rsqrtf(beta);
+    w.sb = beta * w.isb;
     const float betaj = beta + dbeta;
-    w.dsb = dbeta / (sqrtf(betaj) + w.sb);
+    w.isbj = rsqrtf(betaj);
+    // sqrt(beta_j) - sqrt(beta) = dbeta / (sqrt(beta_j) + sqrt(beta))
+    w.dsb = __fdividef(dbeta, betaj * w.isbj + w.sb);
     // ln rho = q1 - ln(beta)/(gamma-1) + beta |u|^2
     if (G14) {
-        const float i2 = isb * isb;
-        w.r = __expf(b.x + beta * uu0) * (i2 * i2 * isb);
+        const float i2 = w.isb * w.isb;
+        w.r = __expf(b.x + beta * uu0) * (i2 * i2 * w.isb);
     } else {
         w.r = __expf(b.x - __logf(beta) * gm1_inv + beta * uu0);
     }
-    const float dlnr = dq.x - log1pf(dbeta / beta) * gm1_inv + (dbeta * uuj + beta * duu);
+    const float dlnr = dq.x - log1pf(dbeta * (2.0f * inv2b)) * gm1_inv + (dbeta * uuj + beta * duu);
     w.dr = w.r * expm1f(dlnr);
     // p = rho / (2 beta):  p_j - p_0 = (drho beta - rho dbeta) / (2 beta beta_j)
     w.p = w.r * inv2b;
-    w.dp = (w.dr * beta - w.r * dbeta) / (2.0f * beta * betaj);
+    w.dp = (w.dr * beta - w.r * dbeta) * (inv2b * (w.isbj * w.isbj));
     return w;
 }
 
@@ -162,8 +169,8 @@ __device__ __forceinline__ float erfc_central_diff(const float m, const float h)
 __device__ __forceinline__ void dsplit_flux_a(const float r0, const float ua0, const float ub0,
                                               const float p0, const float sb0, const float dr,
                                               const float dua, const float dub, const float dp,
-                                              const float dsb, const float sg, const float gm1_inv,
-                                              float dG[4]) {
+                                              const float dsb, const float isb0, const float isbj,
+                                              const float sg, const float gm1_inv, float dG[4]) {
     const float uaj = ua0 + dua, ubj = ub0 + dub, sbj = sb0 + dsb;
     const float S0 = ua0 * sb0;
     const float dS = dua * sbj + ua0 * dsb;
@@ -184,7 +191,6 @@ __device__ __forceinline__ void dsplit_flux_a(const float r0, const float ua0, c
     const float Aj = A0 + dA;
     // B = e / (2 sqrt(pi) sqrt(beta))
     const float c = 0.5f * kInvSqrtPiF;
-    const float isb0 = 1.0f / sb0, isbj = 1.0f / sbj;
     const float B0 = c * e0 * isb0;
     const float dB = c * (de * isbj - e0 * dsb * isbj * isb0);
     const float Bj = B0 + dB;
@@ -219,25 +225,31 @@ __device__ __forceinline__ void dsplit_flux_a(const float r0, const float ua0, c
 }
 
 // q-variables (Eq. 26) from the conserved state, FP64 (the float-pair split
-// below needs q to ~1e-14). With beta = rho/(2p): q2 = 2 beta u1 = m1/p,
-// q3 = m2/p, q4 = -rho/p, beta |u|^2 = (|m|^2 / (2 rho)) / p, and for
-// gamma = 1.4 ln rho + ln(beta)/(gamma-1) = ln(rho beta^2 sqrt(beta)): one
-// logarithm and two reciprocals.
+// below needs q to ~1e-14, a few ulp are fine). With beta = rho/(2p): q2 =
+// 2 beta u1 = m1/p, q3 = m2/p, q4 = -rho/p, beta |u|^2 = |m|^2 / (2 rho p),
+// and for gamma = 1.4 ln rho + ln(beta)/(gamma-1) = ln(rho^2 beta^5) / 2.
+// rho p = (gamma - 1)(rho E - |m|^2/2) needs no division, so 1/rho and 1/p
+// both come from one reciprocal of rho^2 p, and the logarithm needs no
+// square root: this epilogue runs on the FP64 pipe at 1/64 of the FP32 rate.
 template <bool G14>
 __device__ __forceinline__ void cons_to_q64(const V4& U, const Physics& ph, V4& q, double& rho,
                                             double& u, double& v, double& p) {
     rho = U.a;
-    const double irho = 1.0 / rho;
+    const double m2 = fma(U.b, U.b, U.c * U.c);           // |m|^2
+    const double rp = ph.gm1 * fma(U.d, rho, -0.5 * m2);  // rho p
+    const double rr = 1.0 / (rho * rp);                   // 1 / (rho^2 p)
+    const double irho = rp * rr;
+    const double ip = (rho * rho) * rr;
     u = U.b * irho;
     v = U.c * irho;
-    const double ke = 0.5 * (U.b * u + U.c * v);  // rho |u|^2 / 2
-    p = ph.gm1 * (U.d - ke);
-    const double ip = 1.0 / p;
-    const double beta = 0.5 * rho * ip;
+    p = rp * irho;
+    const double bu2 = 0.5 * m2 * (rho * rr);  // beta |u|^2
     if (G14) {
-        q.a = log(rho * (beta * beta) * sqrt(beta)) - ke * ip;
+        const double beta = 0.5 * rho * ip;
+        const double b2 = beta * beta;
+        q.a = 0.5 * log((rho * rho) * (b2 * b2 * beta)) - bu2;
     } else {
-        q.a = log(rho) + log(beta) * ph.gm1_inv - ke * ip;
+        q.a = log(rho) + log(0.5 * rho * ip) * ph.gm1_inv - bu2;
     }
     q.b = U.b * ip;
     q.c = U.c * ip;
@@ -277,7 +289,7 @@ __device__ __forceinline__ double block_sum(double x) {
 // ------------------------------------------------------- flux residual + RK
 
 template <int MODE, int BLOCK, bool G14>
-__global__ void __launch_bounds__(BLOCK) k_flux_mx(const DevGeom g, const DevGeom32 g32,
+__global__ void __launch_bounds__(BLOCK, 896 / BLOCK) k_flux_mx(const DevGeom g, const DevGeom32 g32,
                                                    const Physics ph, const DevState st,
                                                    const QHL* __restrict__ q_in,
                                                    const D8f* __restrict__ dq,
@@ -340,7 +352,7 @@ __global__ void __launch_bounds__(BLOCK) k_flux_mx(const DevGeom g, const DevGeo
                 if (sc) {
                     const float sg = sc == 1u ? 1.f : -1.f;
                     float dG[4];
-                    dsplit_flux_a(w.r, w.u, w.v, w.p, w.sb, w.dr, w.du, w.dv, w.dp, w.dsb, sg,
+                    dsplit_flux_a(w.r, w.u, w.v, w.p, w.sb, w.dr, w.du, w.dv, w.dp, w.dsb, w.isb, w.isbj, sg,
                                   gm1_inv, dG);
                     const float wt = fw.x;
                     R[0] += wt * dG[0]; R[1] += wt * dG[1]; R[2] += wt * dG[2]; R[3] += wt * dG[3];
@@ -348,7 +360,7 @@ __global__ void __launch_bounds__(BLOCK) k_flux_mx(const DevGeom g, const DevGeo
                 if (nc) {
                     const float sg = nc == 1u ? 1.f : -1.f;
                     float dG[4];
-                    dsplit_flux_a(w.r, w.v, w.u, w.p, w.sb, w.dr, w.dv, w.du, w.dp, w.dsb, sg,
+                    dsplit_flux_a(w.r, w.v, w.u, w.p, w.sb, w.dr, w.dv, w.du, w.dp, w.dsb, w.isb, w.isbj, sg,
                                   gm1_inv, dG);
                     const float wt = fw.y;
                     R[0] += wt * dG[0]; R[1] += wt * dG[2]; R[2] += wt * dG[1]; R[3] += wt * dG[3];
@@ -367,10 +379,11 @@ __global__ void __launch_bounds__(BLOCK) k_flux_mx(const DevGeom g, const DevGeo
         } else {
             V4 U = st.U[t];
             double dtv;
-            if (MODE == 1) {
-                const double rho = U.a, u = U.b / rho, v = U.c / rho;
-                const double p = ph.gm1 * (U.d - 0.5 * rho * (u * u + v * v));
-                dtv = ph.cfl * g.dmin[d] / (sqrt(u * u + v * v) + sqrt(ph.gamma * p / rho));
+            if (MODE == 1) {  // local time step (one division, two square roots)
+                const double irho = 1.0 / U.a;
+                const double u = U.b * irho, v = U.c * irho;
+                const double p = ph.gm1 * fma(-0.5 * U.a, fma(u, u, v * v), U.d);
+                dtv = ph.cfl * g.dmin[d] / (sqrt(fma(u, u, v * v)) + sqrt(ph.gamma * p * irho));
                 st.dt[t] = dtv;
                 st.U0[t] = U;
                 r2 = R0 * R0;

@@ -197,6 +197,57 @@ def test_split_flux_kernels_match_fused(c5k):
     assert out[1][2] == out[0][2] + 3 * 4 * 4  # four extra launches per stage
 
 
+def _with_full_stencils(c, points):
+    """The cloud with the given interior points' stencils replaced by their
+    20 nearest other points (the most the library takes)."""
+    import dataclasses
+    nbrs = [list(c.neighbours(i)) for i in range(c.n)]
+    for i in points:
+        d2 = ((c.xy - c.xy[i]) ** 2).sum(1)
+        d2[i] = np.inf
+        nbrs[i] = list(np.argsort(d2, kind="stable")[:20])
+    off = np.zeros(c.n + 1, dtype=np.int32)
+    off[1:] = np.cumsum([len(b) for b in nbrs])
+    idx = np.concatenate([np.asarray(b, dtype=np.int32) for b in nbrs])
+    return dataclasses.replace(c, nbr_offsets=off, nbr_idx=idx)
+
+
+def test_maximum_stencil_size():
+    """Points with the maximum of 20 neighbours (the slot arrays' full depth)."""
+    c0 = Cl.naca0012_cloud(24, 8)
+    interior = np.flatnonzero((c0.flags == 0) & (c0.l == 4))[:5]
+    c = _with_full_stencils(c0, interior)
+    assert np.diff(c.nbr_offsets).max() == 20
+    oc = oracle_for(c)
+    W = Cl.perturbed_state(c, 0.63, 2.0)
+    R_o, tol, spread = residual_conditioning_bound(oc, W)
+    W3, _, st = O.iterate(oc, W, 3)
+    assert st == 0
+    with L.Solver.from_cloud(c) as s:
+        assert s.info()["max_neighbours"] == 20
+        s.set_state(W)
+        R = s.eval_residual()
+        s.step(3)
+        W3g = s.get_state()
+    assert normwise(R, R_o) < tol, (normwise(R, R_o), spread)
+    assert normwise(W3g, W3) < 1e-11
+
+
+@pytest.mark.parametrize("mach", [0.0, 7.5])
+def test_extreme_speed_states(c_ragged, mach):
+    """Still air (S near 0, both signs of tiny velocities) and M 7.5 (|S| up
+    to ~6.3: the library erfc beyond the erfcx table) against the oracle."""
+    oc = oracle_for(c_ragged)
+    W = Cl.perturbed_state(c_ragged, mach, 1.0)
+    R_o, tol, spread = residual_conditioning_bound(oc, W)
+    with L.Solver.from_cloud(c_ragged) as s:
+        s.set_state(W)
+        R = s.eval_residual()
+    print(f"M {mach}: ||R - R_o||/||R_o|| {linf_rel(R, R_o):.2e}, per component "
+          f"{normwise(R, R_o):.2e} (oracle 1-ulp spread {spread:.2e})")
+    assert normwise(R, R_o) < tol, (normwise(R, R_o), spread)
+
+
 def test_tiny_cloud_less_than_two_blocks():
     c = Cl.naca0012_cloud(24, 8)  # 192 points: one full and one ragged block
     oc = oracle_for(c)
