@@ -148,17 +148,20 @@ cudaError_t run_q_derivatives(lskum_ctx* c, int qb, int* final_buf, int64_t* lau
     });
     if (e != cudaSuccess) return e;
     ++*launches;
+    // mixed: dq32[0] <-> dq32[1]; FP64: dq[0] holds the first-order result
+    // for every sweep, which alternate between dq[1] and dq[2]
     int cur = 0;
     for (int it = 0; it < c->opt.inner_iters; ++it) {
+        const int next = c->mixed ? 1 - cur : (cur == 1 ? 2 : 1);
         e = timed(c, kLsInner, [&] {
             return c->mixed ? launch_ls_inner_mx(c->g, c->g32, c->st.qhl[qb], c->st.dq32[cur],
-                                                 c->st.dq32[1 - cur], c->block_ls, c->stream)
-                            : launch_ls_inner(c->g, c->st.q[qb], c->st.dq[cur], c->st.dq[1 - cur],
+                                                 c->st.dq32[next], c->block_ls, c->stream)
+                            : launch_ls_inner(c->g, c->st.dq[0], c->st.dq[cur], c->st.dq[next],
                                               c->block_ls, c->stream);
         });
         if (e != cudaSuccess) return e;
         ++*launches;
-        cur = 1 - cur;
+        cur = next;
     }
     *final_buf = cur;
     return cudaSuccess;
@@ -345,6 +348,12 @@ int lskum_create(int64_t n, const double* xy, const double* normals, const int8_
             (e = upload(c, &g.ws, L.ws)) != cudaSuccess ||
             (e = upload(c, &g.wn, L.wn)) != cudaSuccess)
             return bail(e, "upload of the FP64 cloud layout");
+        std::vector<V4> lcoef(L.lc.size() / 4), lsum(L.lsum.size() / 4);
+        std::memcpy(lcoef.data(), L.lc.data(), L.lc.size() * sizeof(double));
+        std::memcpy(lsum.data(), L.lsum.data(), L.lsum.size() * sizeof(double));
+        if ((e = upload(c, &g.lcoef, lcoef)) != cudaSuccess ||
+            (e = upload(c, &g.lsum, lsum)) != cudaSuccess)
+            return bail(e, "upload of the FP64 inner-sweep coefficients");
     } else {
         // FP32 records per neighbour entry: {wx, wy, hdx, hdy} and {ws, wn, hdx, hdy}
         std::vector<float4> lsw(L.wx.size()), fxw(L.wx.size());
@@ -370,7 +379,8 @@ int lskum_create(int64_t n, const double* xy, const double* normals, const int8_
     } else {
         if ((e = dev_alloc(c, &st.q[1], N)) != cudaSuccess ||
             (e = dev_alloc(c, &st.dq[0], N)) != cudaSuccess ||
-            (e = dev_alloc(c, &st.dq[1], N)) != cudaSuccess)
+            (e = dev_alloc(c, &st.dq[1], N)) != cudaSuccess ||
+            (e = dev_alloc(c, &st.dq[2], N)) != cudaSuccess)
             return bail(e, "FP64 state allocation");
     }
     if ((e = dev_alloc(c, &st.U, N)) != cudaSuccess || (e = dev_alloc(c, &st.U0, N)) != cudaSuccess ||

@@ -35,6 +35,12 @@ struct HostLayout {
     std::vector<double> hdx, hdy;  // half of the global offsets x_j - x_i, y_j - y_i
     std::vector<double> wx, wy;    // full-stencil least-squares weights (Eq. 11)
     std::vector<double> ws, wn;    // split-stencil weights of d/ds and d/dn (Eq. 24)
+    // FP64 inner sweeps (Eq. 29) split as q_x = (first-order q_x) - sum_j wx_j
+    // (hdx_j (qx_j - qx_i) + hdy_j (qy_j - qy_i)), likewise q_y: per slot the
+    // products {wx hdx, wx hdy, wy hdx, wy hdy} (4 per slot, [slot][stride]),
+    // per point their sums over the stencil (4 per point). FP64 layouts only.
+    std::vector<double> lc;
+    std::vector<double> lsum;
     // wall loops for the force integral: device ids and n_i ds_i
     std::vector<int32_t> wall_id;
     std::vector<double> wall_nds;  // n_wall x 2

@@ -240,43 +240,44 @@ __global__ void __launch_bounds__(BLOCK) k_ls_first(const DevGeom g, const V4* _
     dq[t] = o;
 }
 
+// One Jacobi sweep of Eq. 29. With dq~_j = (q_j - q_i) - (hdx_j (qx_j - qx_i)
+// + hdy_j (qy_j - qy_i)) (Eq. 28, hdx = dx/2) the sweep is
+//   q_x = sum_j wx_j (q_j - q_i) - [sum_j (a_j qx_j + b_j qy_j) - (A qx_i + B qy_i)]
+// with a_j = wx_j hdx_j, b_j = wx_j hdy_j, A = sum_j a_j, B = sum_j b_j (and
+// c, d, C, D from wy for q_y). The first sum is the first-order derivative of
+// the same stage (dq_first), so a sweep gathers only the neighbours'
+// derivatives: 4 FMAs per component and neighbour instead of 7 FP64
+// operations. The bracket is ~1e-4 of q_x at 10M points and is formed to
+// ~1e-12 of itself, so q_x keeps FP64 accuracy.
 template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK) k_ls_inner(const DevGeom g, const V4* __restrict__ q,
+__global__ void __launch_bounds__(BLOCK) k_ls_inner(const DevGeom g, const V8* __restrict__ dq_first,
                                                     const V8* __restrict__ din,
                                                     V8* __restrict__ dout) {
     const int64_t t = int64_t(blockIdx.x) * BLOCK + threadIdx.x;  // (point, condition)
     const int64_t d = t >> g.cshift;
     const uint32_t cc = uint32_t(t) & g.cmask;
     if (d >= g.n) return;
-    const V4 qi = ld4(q + t);
-    const V8 di = din[t];
-    const double qiv[4] = {qi.a, qi.b, qi.c, qi.d};
     double ax[4] = {0, 0, 0, 0}, ay[4] = {0, 0, 0, 0};
     const int c = g.cnt[d];
     for (int k = 0; k < c; ++k) {
         const int64_t at = int64_t(k) * g.stride + d;
         const uint32_t j = g.nbr[at] & kIndexMask;
-        const double wx = g.wx[at], wy = g.wy[at];
-        const double hx = g.hdx[at], hy = g.hdy[at];
-        const int64_t tj = sidx(g, j, cc);
-        const V4 qj = ld4(q + tj);
-        const V8 dj = din[tj];
-        const double qjv[4] = {qj.a, qj.b, qj.c, qj.d};
+        const V4 p = g.lcoef[at];
+        const V8 dj = din[sidx(g, j, cc)];
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
-            // dq~ = q~_j - q~_0 (Eq. 28) with q~ = q - (dx q_x + dy q_y) / 2, as
-            // differences of nearby values first (no cancellation), then two FMAs
-            const double dqt =
-                fma(-hx, dj.x[m] - di.x[m], fma(-hy, dj.y[m] - di.y[m], qjv[m] - qiv[m]));
-            ax[m] += wx * dqt;
-            ay[m] += wy * dqt;
+            ax[m] = fma(p.a, dj.x[m], fma(p.b, dj.y[m], ax[m]));
+            ay[m] = fma(p.c, dj.x[m], fma(p.d, dj.y[m], ay[m]));
         }
     }
+    const V4 S = g.lsum[d];
+    const V8 di = din[t];
+    const V8 f = dq_first[t];
     V8 o;
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-        o.x[m] = ax[m];
-        o.y[m] = ay[m];
+        o.x[m] = f.x[m] - (ax[m] - fma(S.a, di.x[m], S.b * di.y[m]));
+        o.y[m] = f.y[m] - (ay[m] - fma(S.c, di.x[m], S.d * di.y[m]));
     }
     dout[t] = o;
 }
@@ -726,12 +727,13 @@ cudaError_t launch_ls_first(const DevGeom& g, const V4* q, V8* dq, int block, cu
     return cudaGetLastError();
 }
 
-cudaError_t launch_ls_inner(const DevGeom& g, const V4* q, const V8* din, V8* dout, int block,
+cudaError_t launch_ls_inner(const DevGeom& g, const V8* dq_first, const V8* din, V8* dout, int block,
                             cudaStream_t s) {
     if (block == 256)
-        k_ls_inner<256><<<grid_nc(g, 256), 256, 0, s>>>(g, q, din, dout);
+        k_ls_inner<256><<<grid_nc(g, 256), 256, 0, s>>>(g, dq_first, din, dout);
     else
-        k_ls_inner<kDefaultBlock><<<grid_nc(g, kDefaultBlock), kDefaultBlock, 0, s>>>(g, q, din, dout);
+        k_ls_inner<kDefaultBlock><<<grid_nc(g, kDefaultBlock), kDefaultBlock, 0, s>>>(g, dq_first, din,
+                                                                                     dout);
     return cudaGetLastError();
 }
 

@@ -62,6 +62,10 @@ struct DevGeom {
     const double* wy;
     const double* ws;
     const double* wn;
+    // FP64 inner sweeps: per slot {wx hdx, wx hdy, wy hdx, wy hdy}, per point
+    // their sums over the stencil
+    const V4* lcoef;
+    const V4* lsum;
     const int32_t* dev_to_user;
     const int32_t* user_to_dev;
     int64_t n_wall;
@@ -84,7 +88,8 @@ struct DevState {
     V4* U;     // conserved state
     V4* U0;    // state at the start of the iteration
     V4* q[2];  // q-variables, double-buffered across stages
-    V8* dq[2]; // q-derivatives, double-buffered across inner iterations
+    V8* dq[3]; // q-derivatives: [0] first order (kept for the FP64 inner sweeps),
+               // [1], [2] alternate across inner iterations
     double* dt;
     QHL* qhl[2];  // mixed precision: q-variables as float pairs
     D8f* dq32[2]; // mixed precision: q-derivatives in FP32
@@ -112,7 +117,7 @@ __host__ __device__ __forceinline__ int64_t sidx(const DevGeom& g, int64_t d, ui
 
 // Launchers (return cudaGetLastError()).
 cudaError_t launch_ls_first(const DevGeom& g, const V4* q, V8* dq, int block, cudaStream_t s);
-cudaError_t launch_ls_inner(const DevGeom& g, const V4* q, const V8* dq_in, V8* dq_out, int block,
+cudaError_t launch_ls_inner(const DevGeom& g, const V8* dq_first, const V8* dq_in, V8* dq_out, int block,
                             cudaStream_t s);
 // mode 0: evaluate R only (written to st.R); mode 1..4: SSP-RK stage.
 cudaError_t launch_flux(int mode, const DevGeom& g, const Physics& ph, const DevState& st,

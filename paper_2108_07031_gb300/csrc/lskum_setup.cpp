@@ -13,7 +13,8 @@
 //       split stencil (Eq. 24):  dG/ds = sum_j ws_j dG_j, dG/dn = sum_j wn_j dG_j
 //     i.e. the rows of the 2x2 inverse applied to (dx_j, dy_j), so the device
 //     never forms or inverts the 2x2 matrices; the specular wall's factor on
-//     dGn-/dn is folded into wn.
+//     dGn-/dn is folded into wn. For the FP64 inner sweeps also the products
+//     wx hdx, wx hdy, wy hdx, wy hdy per slot and their sums per point.
 //  4. Wall loops and their n_i ds_i for the force integral.
 //
 // Compiled with -ffp-contract=off: the stencil-membership signs must be the
@@ -172,6 +173,11 @@ int build_layout(int64_t n, const double* xy, const double* normals, const int8_
     L.wy.assign(size_t(slots) * S, 0.0);
     L.ws.assign(size_t(slots) * S, 0.0);
     L.wn.assign(size_t(slots) * S, 0.0);
+    const bool want_lc = opt.precision == LSKUM_FP64;
+    if (want_lc) {
+        L.lc.assign(size_t(slots) * S * 4, 0.0);
+        L.lsum.assign(size_t(n) * 4, 0.0);
+    }
 
     int64_t bad_point = -1;
     const char* bad_what = "";
@@ -273,6 +279,14 @@ int build_layout(int64_t n, const double* xy, const double* normals, const int8_
             L.wy[at] = wt[k] * (dy[k] * sxx - dx[k] * sxy) / det;
             L.ws[at] = ws;
             L.wn[at] = wn;
+            if (want_lc) {
+                double* c4 = &L.lc[4 * at];
+                c4[0] = L.wx[at] * L.hdx[at];
+                c4[1] = L.wx[at] * L.hdy[at];
+                c4[2] = L.wy[at] * L.hdx[at];
+                c4[3] = L.wy[at] * L.hdy[at];
+                for (int m = 0; m < 4; ++m) L.lsum[4 * d + m] += c4[m];
+            }
         }
     }
     if (bad_point >= 0) {
