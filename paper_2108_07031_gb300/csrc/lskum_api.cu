@@ -148,13 +148,13 @@ cudaError_t run_q_derivatives(lskum_ctx* c, int qb, int* final_buf, int64_t* lau
     });
     if (e != cudaSuccess) return e;
     ++*launches;
-    // mixed: dq32[0] <-> dq32[1]; FP64: dq[0] holds the first-order result
-    // for every sweep, which alternate between dq[1] and dq[2]
+    // buffer 0 holds the first-order result, used by every sweep; the
+    // sweeps alternate between buffers 1 and 2
     int cur = 0;
     for (int it = 0; it < c->opt.inner_iters; ++it) {
-        const int next = c->mixed ? 1 - cur : (cur == 1 ? 2 : 1);
+        const int next = cur == 1 ? 2 : 1;
         e = timed(c, kLsInner, [&] {
-            return c->mixed ? launch_ls_inner_mx(c->g, c->g32, c->st.qhl[qb], c->st.dq32[cur],
+            return c->mixed ? launch_ls_inner_mx(c->g, c->g32, c->st.dq32[0], c->st.dq32[cur],
                                                  c->st.dq32[next], c->block_ls, c->stream)
                             : launch_ls_inner(c->g, c->st.dq[0], c->st.dq[cur], c->st.dq[next],
                                               c->block_ls, c->stream);
@@ -374,7 +374,8 @@ int lskum_create(int64_t n, const double* xy, const double* normals, const int8_
         if ((e = dev_alloc(c, &st.qhl[0], N)) != cudaSuccess ||
             (e = dev_alloc(c, &st.qhl[1], N)) != cudaSuccess ||
             (e = dev_alloc(c, &st.dq32[0], N)) != cudaSuccess ||
-            (e = dev_alloc(c, &st.dq32[1], N)) != cudaSuccess)
+            (e = dev_alloc(c, &st.dq32[1], N)) != cudaSuccess ||
+            (e = dev_alloc(c, &st.dq32[2], N)) != cudaSuccess)
             return bail(e, "mixed-precision state allocation");
     } else {
         if ((e = dev_alloc(c, &st.q[1], N)) != cudaSuccess ||

@@ -92,7 +92,7 @@ struct DevState {
                // [1], [2] alternate across inner iterations
     double* dt;
     QHL* qhl[2];  // mixed precision: q-variables as float pairs
-    D8f* dq32[2]; // mixed precision: q-derivatives in FP32
+    D8f* dq32[3]; // mixed precision: q-derivatives in FP32, [0] first order, [1], [2] sweeps
     V4* R;     // residual output of the evaluation mode
     double* partials;  // per-block partial sums (scratch)
     double* r2;        // C > 1: stage-1 R_rho^2 per (point, condition) (scratch)
@@ -145,8 +145,8 @@ cudaError_t launch_forces(const DevGeom& g, const Physics& ph, const DevState& s
 // Mixed-precision launchers (lskum_kernels_mixed.cu).
 cudaError_t launch_ls_first_mx(const DevGeom& g, const DevGeom32& g32, const QHL* q, D8f* dq,
                                int block, cudaStream_t s);
-cudaError_t launch_ls_inner_mx(const DevGeom& g, const DevGeom32& g32, const QHL* q,
-                               const D8f* din, D8f* dout, int block, cudaStream_t s);
+cudaError_t launch_ls_inner_mx(const DevGeom& g, const DevGeom32& g32, const D8f* dq_first,
+                               const D8f* dq_in, D8f* dq_out, int block, cudaStream_t s);
 cudaError_t launch_flux_mx(int mode, const DevGeom& g, const DevGeom32& g32, const Physics& ph,
                            const DevState& st, const QHL* q_in, const D8f* dq, QHL* q_out,
                            int block, cudaStream_t s);

@@ -65,16 +65,20 @@ __global__ void __launch_bounds__(BLOCK) k_ls_first_mx(const DevGeom g, const De
     dq[t] = D8f{ax, ay};
 }
 
+// One Jacobi sweep of Eq. 29 as the first-order derivative of the stage
+// (dq_first, the sum of wx_j (q_j - q_i)) minus the sum of wx_j (hdx_j
+// (qx_j - qx_i) + hdy_j (qy_j - qy_i)): the q gathers and their float-pair
+// differences are done once per stage, not per sweep; the derivative
+// differences stay differences (exact in FP32 for nearby values).
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK) k_ls_inner_mx(const DevGeom g, const DevGeom32 g32,
-                                                       const QHL* __restrict__ q,
+                                                       const D8f* __restrict__ dq_first,
                                                        const D8f* __restrict__ din,
                                                        D8f* __restrict__ dout) {
     const int64_t t = int64_t(blockIdx.x) * BLOCK + threadIdx.x;  // (point, condition)
     const int64_t d = t >> g.cshift;
     const uint32_t cc = uint32_t(t) & g.cmask;
     if (d >= g.n) return;
-    const QHL qi = q[t];
     const D8f di = din[t];
     float4 ax = make_float4(0.f, 0.f, 0.f, 0.f), ay = ax;
     const int c = g.cnt[d];
@@ -83,18 +87,18 @@ __global__ void __launch_bounds__(BLOCK) k_ls_inner_mx(const DevGeom g, const De
         const uint32_t j = g.nbr[at] & kIndexMask;
         const float4 lw = g32.lsw[at];
         const float wx = lw.x, wy = lw.y, hx = lw.z, hy = lw.w;
-        const int64_t jt = sidx(g, j, cc);
-        const float4 dqv = qdiff(q[jt], qi);
-        const D8f dj = din[jt];
-        // dq~ = (q_j - q_i) - (dx (qx_j - qx_i) + dy (qy_j - qy_i)) / 2   (Eq. 28)
-        const float t0 = dqv.x - (hx * (dj.x.x - di.x.x) + hy * (dj.y.x - di.y.x));
-        const float t1 = dqv.y - (hx * (dj.x.y - di.x.y) + hy * (dj.y.y - di.y.y));
-        const float t2 = dqv.z - (hx * (dj.x.z - di.x.z) + hy * (dj.y.z - di.y.z));
-        const float t3 = dqv.w - (hx * (dj.x.w - di.x.w) + hy * (dj.y.w - di.y.w));
+        const D8f dj = din[sidx(g, j, cc)];
+        // (dx (qx_j - qx_i) + dy (qy_j - qy_i)) / 2, the Eq. 28 correction
+        const float t0 = hx * (dj.x.x - di.x.x) + hy * (dj.y.x - di.y.x);
+        const float t1 = hx * (dj.x.y - di.x.y) + hy * (dj.y.y - di.y.y);
+        const float t2 = hx * (dj.x.z - di.x.z) + hy * (dj.y.z - di.y.z);
+        const float t3 = hx * (dj.x.w - di.x.w) + hy * (dj.y.w - di.y.w);
         ax.x += wx * t0; ax.y += wx * t1; ax.z += wx * t2; ax.w += wx * t3;
         ay.x += wy * t0; ay.y += wy * t1; ay.z += wy * t2; ay.w += wy * t3;
     }
-    dout[t] = D8f{ax, ay};
+    const D8f f = dq_first[t];
+    dout[t] = D8f{make_float4(f.x.x - ax.x, f.x.y - ax.y, f.x.z - ax.z, f.x.w - ax.w),
+                  make_float4(f.y.x - ay.x, f.y.y - ay.y, f.y.z - ay.z, f.y.w - ay.w)};
 }
 
 // ------------------------------------------------ primitive base + difference
@@ -483,12 +487,13 @@ cudaError_t launch_ls_first_mx(const DevGeom& g, const DevGeom32& g32, const QHL
     return cudaGetLastError();
 }
 
-cudaError_t launch_ls_inner_mx(const DevGeom& g, const DevGeom32& g32, const QHL* q,
+cudaError_t launch_ls_inner_mx(const DevGeom& g, const DevGeom32& g32, const D8f* dq_first,
                                const D8f* din, D8f* dout, int block, cudaStream_t s) {
     if (block == 256)
-        k_ls_inner_mx<256><<<grid_nc(g, 256), 256, 0, s>>>(g, g32, q, din, dout);
+        k_ls_inner_mx<256><<<grid_nc(g, 256), 256, 0, s>>>(g, g32, dq_first, din, dout);
     else
-        k_ls_inner_mx<kDefaultBlock><<<grid_nc(g, kDefaultBlock), kDefaultBlock, 0, s>>>(g, g32, q, din, dout);
+        k_ls_inner_mx<kDefaultBlock><<<grid_nc(g, kDefaultBlock), kDefaultBlock, 0, s>>>(g, g32, dq_first,
+                                                                                        din, dout);
     return cudaGetLastError();
 }
 
