@@ -57,10 +57,12 @@ EXPORTED = ("lskum_mlp_num_params", "lskum_mlp_create", "lskum_mlp_destroy",
             "lskum_mlp_predict", "lskum_mlp_gradients", "lskum_mlp_train_step", "lskum_mlp_sync")
 
 
-def projection(seed: int = 2108) -> np.ndarray:
-    """Seeded 8 x 2 Gaussian projection of (x, y) for the Fourier features."""
+def projection(seed: int = 2108, scales=(1.0,) * 8) -> np.ndarray:
+    """Seeded 8 x 2 Gaussian projection of (x, y) for the Fourier features;
+    row k has standard deviation scales[k] (its spatial frequency)."""
     rng = np.random.Generator(np.random.PCG64(seed))
-    return rng.normal(0.0, 1.0, size=(8, 2)).astype(np.float32)
+    P = rng.normal(0.0, 1.0, size=(8, 2))
+    return (P * np.asarray(scales, dtype=np.float64)[:, None]).astype(np.float32)
 
 
 def init_params(seed: int = 0) -> np.ndarray:
@@ -238,14 +240,15 @@ def train(mlp: MLP, feats_dev, targets_dev, epochs=40, batch=8192, lr=2e-3, lr_f
     losses = []
     for ep in range(epochs):
         perm = torch.randperm(n, generator=g).to(feats_dev.device)
-        ep_loss = 0.0
         for k in range(steps_per_epoch):
             idx = perm[k * batch:(k + 1) * batch]
             lr_k = lr_final + 0.5 * (lr - lr_final) * (1 + math.cos(math.pi * step / total))
-            loss = mlp.train_step(feats_dev[idx].contiguous(), targets_dev[idx].contiguous(), lr_k)
-            ep_loss += loss
+            # the loss is read back (a host synchronisation) once per epoch
+            last = k == steps_per_epoch - 1
+            loss = mlp.train_step(feats_dev[idx].contiguous(), targets_dev[idx].contiguous(), lr_k,
+                                  want_loss=last)
             step += 1
-        losses.append(ep_loss / steps_per_epoch)
+        losses.append(loss)  # loss of the epoch's last mini-batch
         if log:
             log(f"epoch {ep}: loss {losses[-1]:.3e}")
     return losses

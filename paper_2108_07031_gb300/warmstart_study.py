@@ -18,6 +18,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import os
 import time
 
 import numpy as np
@@ -38,6 +39,11 @@ def main():
     ap.add_argument("--eval-cfl", type=float, default=0.2)
     ap.add_argument("--eval-iters", type=int, default=60_000)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--proj-scales", default="1,1,1,1,1,1,1,1",
+                    help="standard deviations of the 8 Fourier projections")
+    ap.add_argument("--batch", type=int, default=8192)
+    ap.add_argument("--data-cache", default="",
+                    help="file (.npy) to keep the converged training states in between runs")
     args = ap.parse_args()
     prec = L.MIXED if args.precision == "mixed" else L.FP64
     log = lambda m: print(m, flush=True)  # noqa: E731
@@ -47,17 +53,23 @@ def main():
     m_tr, a_tr = Cl.conditions(args.train, seed=2021)
     m_te, a_te = Cl.conditions(args.test, seed=4242)
     t0 = time.time()
-    W_tr, it_tr = S.converged_solutions(cloud, m_tr, a_tr, tol=1e-7, max_iters=40_000)
+    if args.data_cache and os.path.exists(args.data_cache):
+        W_tr, it_tr = np.load(args.data_cache), []
+    else:
+        W_tr, it_tr = S.converged_solutions(cloud, m_tr, a_tr, tol=1e-7, max_iters=40_000)
+        if args.data_cache:
+            np.save(args.data_cache, W_tr)
     t_data = time.time() - t0
     log(f"training data: {args.train} conditions in {t_data:.1f} s (iterations per batch {it_tr})")
 
     raw = np.concatenate(S.raw_inputs(cloud, wd, m_tr, a_tr))
     T = np.concatenate([S.targets(W_tr[k], m_tr[k], a_tr[k]) for k in range(args.train)])
-    net = S.MLP(capacity=16384, seed=0)
+    scales = [float(v) for v in args.proj_scales.split(",")]
+    net = S.MLP(capacity=16384, seed=0, proj=S.projection(scales=scales))
     feats = net.features(torch.from_numpy(raw).cuda())
     Td = torch.from_numpy(T).cuda()
     t0 = time.time()
-    losses = S.train(net, feats, Td, epochs=args.epochs, batch=8192, lr=2e-3, lr_final=2e-5,
+    losses = S.train(net, feats, Td, epochs=args.epochs, batch=args.batch, lr=2e-3, lr_final=2e-5,
                      log=log)
     t_train = time.time() - t0
 
@@ -107,7 +119,8 @@ def main():
                       np.abs(results["cold"]["W"][k]).max()) for k in range(n)]
     out = {
         "cloud_points": cloud.n, "train_conditions": args.train, "test_conditions": n,
-        "eval_cfl": args.eval_cfl, "precision": args.precision,
+        "eval_cfl": args.eval_cfl, "precision": args.precision, "proj_scales": scales,
+        "epochs": args.epochs,
         "data_seconds": t_data, "train_seconds": t_train,
         "loss_first": losses[0], "loss_last": losses[-1], "fallbacks": fallback,
         "iterations_cold": it_cold.tolist(), "iterations_warm": it_warm.tolist(),
