@@ -60,7 +60,7 @@ def workload_config(points_requested: int, world: int, flux_split: bool = False)
     return {"workload": f"naca0012-o-cloud-{n}pts-fp64" + ("-split-flux-kernels" if flux_split else ""),
             "points": n, "mach": MACH, "alpha_deg": ALPHA, "inner_iters": 2, "rk_stages": 4,
             "cfl": 0.2, "parallelism": f"replicas{world}",
-            "l2": "inputs larger than L2 (device working set ~12 GB), no flush",
+            "l2": "inputs larger than L2 (device working set ~17 GB), no flush",
             "initial_state": "developed: seeded smooth perturbation of the free stream at every "
                              "point"}
 
