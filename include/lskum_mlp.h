@@ -71,12 +71,25 @@ int lskum_mlp_gradients(lskum_mlp* h, const float* feat_dev, const float* target
                         float* grads, double* loss);
 
 /* One Adam step (beta 0.9 / 0.999, eps 1e-8, learning rate lr) on the batch;
- * *loss (may be NULL) receives the batch loss before the step. */
+ * *loss (may be NULL) receives the batch loss before the step. With loss
+ * NULL the call returns once the work is queued on the handle's stream: the
+ * caller keeps feat_dev and target_dev unchanged until that stream has run
+ * it (lskum_mlp_sync, or order its own writes after it by running on the
+ * same stream, see lskum_mlp_set_stream). With loss non-NULL it returns
+ * after the step. */
 int lskum_mlp_train_step(lskum_mlp* h, const float* feat_dev, const float* target_dev, int64_t n,
                          float lr, double* loss);
 
 /* Waits for the handle's stream. */
 int lskum_mlp_sync(lskum_mlp* h);
+
+/* Runs the handle's work on the caller's CUDA stream (a cudaStream_t; NULL
+ * restores the handle's own stream). Work the caller queues on the same
+ * stream -- refilling the batch buffers of lskum_mlp_train_step, say -- is
+ * then ordered after the handle's. Waits for the previous stream first.
+ * For the legacy default stream pass cudaStreamLegacy ((void*)0x1).
+ * No counterpart in the paper (the warm start is not part of the method). */
+int lskum_mlp_set_stream(lskum_mlp* h, void* stream);
 
 #ifdef __cplusplus
 }

@@ -465,7 +465,8 @@ __global__ void k_weights_bf16(const float* __restrict__ p, LayerPtrs L) {
 using namespace mlpk;
 
 struct lskum_mlp {
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;      // stream the handle's work runs on
+    cudaStream_t own_stream = nullptr;  // the handle's own (created, destroyed by it)
     int64_t cap = 0;  // samples per call
     int64_t nparam = 0;
     LayerPtrs L{};
@@ -668,12 +669,13 @@ int lskum_mlp_create(int64_t capacity, const float* proj, lskum_mlp** out) {
     h->nparam = lskum_mlp_num_params();
     auto bail = [&](cudaError_t e) {
         for (void* p : h->allocs) cudaFree(p);
-        if (h->stream) cudaStreamDestroy(h->stream);
+        if (h->own_stream) cudaStreamDestroy(h->own_stream);
         delete h;
         return fail(LSKUM_ERR_CUDA, std::string("lskum_mlp_create: ") + cudaGetErrorString(e));
     };
     cudaError_t e;
-    if ((e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking)) != cudaSuccess) return bail(e);
+    if ((e = cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking)) != cudaSuccess) return bail(e);
+    h->stream = h->own_stream;
     int64_t off = 0;
     for (int l = 0; l < kLayers; ++l) {
         h->L.w_off[l] = off;
@@ -710,7 +712,7 @@ void lskum_mlp_destroy(lskum_mlp* h) {
     if (!h) return;
     cudaStreamSynchronize(h->stream);
     for (void* p : h->allocs) cudaFree(p);
-    cudaStreamDestroy(h->stream);
+    cudaStreamDestroy(h->own_stream);
     delete h;
 }
 
@@ -792,6 +794,13 @@ int lskum_mlp_train_step(lskum_mlp* h, const float* feat, const float* target, i
 int lskum_mlp_sync(lskum_mlp* h) {
     if (!h) return fail(LSKUM_ERR_INVALID_ARG, "null");
     MLP_CUDA(cudaStreamSynchronize(h->stream));
+    return LSKUM_OK;
+}
+
+int lskum_mlp_set_stream(lskum_mlp* h, void* stream) {
+    if (!h) return fail(LSKUM_ERR_INVALID_ARG, "null");
+    MLP_CUDA(cudaStreamSynchronize(h->stream));
+    h->stream = stream ? static_cast<cudaStream_t>(stream) : h->own_stream;
     return LSKUM_OK;
 }
 

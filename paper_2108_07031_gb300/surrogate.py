@@ -43,6 +43,7 @@ def _lib():
             "lskum_mlp_gradients": ([P, P, P, I64, P, P], I),
             "lskum_mlp_train_step": ([P, P, P, I64, F, P], I),
             "lskum_mlp_sync": ([P], I),
+            "lskum_mlp_set_stream": ([P, P], I),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -54,7 +55,8 @@ def _lib():
 
 EXPORTED = ("lskum_mlp_num_params", "lskum_mlp_create", "lskum_mlp_destroy",
             "lskum_mlp_set_params", "lskum_mlp_get_params", "lskum_mlp_features",
-            "lskum_mlp_predict", "lskum_mlp_gradients", "lskum_mlp_train_step", "lskum_mlp_sync")
+            "lskum_mlp_predict", "lskum_mlp_gradients", "lskum_mlp_train_step", "lskum_mlp_sync",
+            "lskum_mlp_set_stream")
 
 
 def projection(seed: int = 2108, scales=(1.0,) * 8) -> np.ndarray:
@@ -98,6 +100,17 @@ class MLP:
         self._h = h
         self.n_params = int(lib.lskum_mlp_num_params())
         self.set_params(init_params(seed))
+        # run on torch's current stream: the batches torch gathers for
+        # train_step are then written only after the previous step read them
+        import torch
+        if torch.cuda.is_available():
+            self.set_stream(torch.cuda.current_stream().cuda_stream)
+
+    def set_stream(self, handle: int):
+        """Run on CUDA stream `handle` (torch's `cuda_stream`; 0, the legacy
+        default stream, is passed as cudaStreamLegacy)."""
+        h = int(handle) if handle else 1  # 1 == cudaStreamLegacy
+        L._check(self._lib.lskum_mlp_set_stream(self._h, C.c_void_p(h)), "lskum_mlp_set_stream")
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
