@@ -35,7 +35,7 @@ def main():
     ap.add_argument("--out", default="warmstart_study.json")
     ap.add_argument("--train", type=int, default=256)
     ap.add_argument("--test", type=int, default=32)
-    ap.add_argument("--epochs", type=int, default=80)
+    ap.add_argument("--epochs", type=int, default=240)
     ap.add_argument("--eval-cfl", type=float, default=0.2)
     ap.add_argument("--eval-iters", type=int, default=60_000)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
