@@ -499,3 +499,29 @@ def test_residue_decays_on_5k_cloud(cloud5k, oc5k):
     assert res[0] == 0.0  # a uniform state has zero residual
     assert res[-1] < 0.35 * res[1:20].max()
     assert np.all(np.isfinite(W)) and np.all(W[:, 0] > 0) and np.all(W[:, 3] > 0)
+
+
+# ------------------------------------------------------- regression guard
+
+def test_oracle_matches_its_stored_regression_values():
+    """The oracle's results on a small seeded case equal the values stored by
+    tests/golden/make_oracle_regression.py (a guard against accidental
+    changes of its arithmetic; libm may differ by an ulp across machines,
+    which the split-flux differences amplify to ~1e-13)."""
+    import json
+    import os
+    import sys
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    sys.path.insert(0, here)
+    import make_oracle_regression as G
+    with open(os.path.join(here, "oracle_regression.json")) as f:
+        ref = json.load(f)
+    now = G.compute()
+    R, R_ref = np.array(now["residual_of_perturbed_state"]), np.array(ref["residual_of_perturbed_state"])
+    assert np.abs(R - R_ref).max() <= 1e-10 * np.abs(R_ref).max()
+    a, b = now["iterate_50_from_freestream"], ref["iterate_50_from_freestream"]
+    assert a["status"] == b["status"] == 0
+    W, W_ref = np.array(a["state"]), np.array(b["state"])
+    assert np.abs(W - W_ref).max() <= 1e-10 * np.abs(W_ref).max()
+    assert abs(a["cl"] - b["cl"]) <= 1e-10 and abs(a["cd"] - b["cd"]) <= 1e-10
+    assert np.allclose(a["residue"], b["residue"], rtol=1e-9, atol=0)
