@@ -15,6 +15,10 @@ basis of the local variable; the script checks the relative error of every
 piece at 2000 points in double-precision Horner evaluation and refuses to
 write the header unless it is below 4e-16.
 
+   The mixed-precision path evaluates the same function in FP32 from its own
+   table: 24 pieces of width 1/4 and degree 5 (checked below 3e-7 relative
+   in float32 Horner evaluation).
+
 2. The exponential by Tang's table-driven method: x = k ln2/64 + r with
 |r| <= ln2/128, exp(x) = 2^(k div 64) * 2^((k mod 64)/64) * e^r; the table
 holds 2^(j/64), j < 64, correctly rounded (mpmath), and ln2/64 is split into
@@ -32,6 +36,7 @@ mp.mp.dps = 50
 
 CX_LO, CX_HI, CX_W = 0.0, 6.0, 0.125
 CX_DEG = 9            # degree in z = a - c on [-1/16, 1/16]
+CXF_W, CXF_DEG = 0.25, 5  # FP32 table (mixed precision)
 
 
 def cheb_to_monomial(f, lo, hi, deg, shift):
@@ -54,6 +59,36 @@ def horner(c, z):
     for k in range(len(c) - 2, -1, -1):
         r = r * z + float(c[k])
     return r
+
+
+def horner_f32(c, z):
+    c = [np.float32(float(v)) for v in c]
+    r = np.zeros_like(z, dtype=np.float32) + c[-1]
+    for k in range(len(c) - 2, -1, -1):
+        r = (r * z + c[k]).astype(np.float32)
+    return r
+
+
+def erfcx_pieces_f32():
+    """FP32 pieces of erfcx on [CX_LO, CX_HI]: (centres, coefficients, worst error)."""
+    centres, pieces, worst = [], [], 0.0
+    a = CX_LO
+    while a < CX_HI - 1e-12:
+        lo, hi = a, a + CXF_W
+        c = (lo + hi) / 2
+        C = cheb_to_monomial(lambda u: mp.erfc(u) * mp.exp(u * u), mp.mpf(lo), mp.mpf(hi), CXF_DEG,
+                             mp.mpf(c))
+        zs = np.linspace(lo, hi, 500)
+        ref = np.array([float(mp.erfc(mp.mpf(float(u))) * mp.exp(mp.mpf(float(u)) ** 2))
+                        for u in zs])
+        got = horner_f32(C, (zs.astype(np.float32) - np.float32(c)).astype(np.float32))
+        e = np.max(np.abs(got - ref) / np.abs(ref))
+        assert e < 3e-7, ("erfcx f32", lo, e)
+        worst = max(worst, e)
+        centres.append(c)
+        pieces.append([float(np.float32(float(x))) for x in C])
+        a = hi
+    return centres, pieces, worst
 
 
 def main():
@@ -95,6 +130,15 @@ def main():
         f.write("__device__ const double kErfcxC[kErfcxPieces][kErfcxDeg + 2] = {\n")
         for c, p in zip(centres, pieces):
             f.write("    {" + f"{c!r}, " + ", ".join(repr(x) for x in p) + "},\n")
+        f.write("};\n\n")
+        fc, fp, fworst = erfcx_pieces_f32()
+        f.write(f"// FP32 erfcx pieces (mixed precision): width {CXF_W}, degree {CXF_DEG}, "
+                f"max relative error {fworst:.2e} in float32 Horner.\n")
+        f.write(f"constexpr float kErfcxFInvW = {1.0 / CXF_W!r}f;\n")
+        f.write(f"constexpr int kErfcxFPieces = {len(fp)};\nconstexpr int kErfcxFDeg = {CXF_DEG};\n")
+        f.write("__device__ const float kErfcxF[kErfcxFPieces][kErfcxFDeg + 2] = {\n")
+        for c, p in zip(fc, fp):
+            f.write("    {" + f"{c!r}f, " + ", ".join(f"{x!r}f" for x in p) + "},\n")
         f.write("};\n\n")
         f.write("// exp(x) by Tang's table-driven reduction: 2^(j/64), j < 64, correctly rounded,\n")
         f.write("// and ln2/64 = kLn2By64Hi + kLn2By64Lo.\n")
