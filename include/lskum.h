@@ -124,7 +124,8 @@ int lskum_create(int64_t n, const double* xy, const double* normals, const int8_
 void lskum_destroy(lskum_ctx* ctx);
 
 /* Issues all later work of ctx on `stream` (a cudaStream_t; NULL = the
- * context's own stream). The caller keeps the stream alive while in use. */
+ * context's own stream; the legacy default stream is cudaStreamLegacy). The
+ * caller keeps the stream alive while in use. */
 int lskum_set_stream(lskum_ctx* ctx, void* stream);
 
 /* Free stream rho = 1, p = 1/gamma, u = mach (cos a, sin a), alpha in degrees;
