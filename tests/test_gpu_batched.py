@@ -77,6 +77,32 @@ def test_set_state_and_residual_layout(cloud):
         assert normwise(R[k], R_o) < tol, (normwise(R[k], R_o), spread)
 
 
+@pytest.mark.parametrize("opts", [dict(weight_power=1.5, inner_iters=3),
+                                  dict(order=1, inner_iters=0), dict(outer_mode=0)])
+def test_batched_option_variants_against_oracle(cloud, opts):
+    """Options apply to every condition of a batch: 4 conditions with
+    least-squares weights / first-order LSKUM / the kinetic far field, the
+    residual of each developed state against the oracle with the same
+    options, then 3 iterations."""
+    ok = {k: v for k, v in opts.items() if k in ("order", "outer_mode", "weight_power")}
+    inner = opts.get("inner_iters", 2)
+    oc = O.OracleCloud.from_cloud(cloud, **ok)
+    mach, alpha = Cl.conditions(4, seed=77)
+    W = np.stack([Cl.perturbed_state(cloud, mach[k], alpha[k], seed=k + 1) for k in range(4)])
+    with L.Solver.from_cloud(cloud, n_conditions=4, **opts) as b:
+        b.set_conditions(mach, alpha)
+        b.set_state(W)
+        R = b.eval_residual()
+        b.step(3)
+        W3 = b.get_state()
+    for k in (0, 3):
+        R_o, tol, spread = residual_conditioning_bound(oc, W[k], inner=inner)
+        assert normwise(R[k], R_o) < tol, (k, normwise(R[k], R_o), spread)
+        W3_o, _, st = O.iterate(oc, W[k], 3, inner=inner)
+        assert st == 0
+        assert normwise(W3[k], W3_o) < 1e-11
+
+
 def test_set_conditions_checks_count(cloud):
     with L.Solver.from_cloud(cloud, n_conditions=4) as b:
         with pytest.raises(L.LskumError) as e:
