@@ -185,6 +185,39 @@ def wall_distance(cloud) -> np.ndarray:
     return d
 
 
+def wall_arc(cloud) -> np.ndarray:
+    """Position (0..1) along the wall loop of every point's nearest wall point."""
+    wall_idx = np.flatnonzero(cloud.flags == Cl.FLAG_WALL)
+    walls = cloud.xy[wall_idx]
+    s = np.empty(cloud.n)
+    for a in range(0, cloud.n, 4096):
+        diff = cloud.xy[a:a + 4096, None, :] - walls[None, :, :]
+        s[a:a + 4096] = np.argmin((diff ** 2).sum(-1), axis=1) / float(len(wall_idx))
+    return s
+
+
+def wall_features(cloud, wall_d, arc, mach, alpha_deg, proj) -> np.ndarray:
+    """Alternative 21 (+ 11 zero) inputs, computed on the host: (x, y, wall
+    distance, M, alpha) scaled as in lskum_mlp_features, then sin/cos of
+    2 pi k s (k = 1..4) of the wall-loop position s of the nearest wall
+    point, then sin/cos of the first 4 Fourier projections of (x, y).
+    n x 32 float32."""
+    x, y = cloud.xy[:, 0], cloud.xy[:, 1]
+    f = np.zeros((cloud.n, 32))
+    f[:, 0] = x / 10.0
+    f[:, 1] = y / 10.0
+    f[:, 2] = np.log(wall_d + 1e-3) / 5.0
+    f[:, 3] = (mach - 0.55) * 4.0
+    f[:, 4] = (alpha_deg - 1.0) / 5.0
+    for k in range(4):
+        f[:, 5 + k] = np.sin(2 * np.pi * (k + 1) * arc)
+        f[:, 9 + k] = np.cos(2 * np.pi * (k + 1) * arc)
+    t = cloud.xy @ np.asarray(proj, dtype=np.float64)[:4].T
+    f[:, 13:17] = np.sin(t)
+    f[:, 17:21] = np.cos(t)
+    return f.astype(np.float32)
+
+
 def raw_inputs(cloud, wall_d, mach, alpha_deg) -> np.ndarray:
     """n_cond x n x 5 float32: (x, y, wall distance, M, alpha)."""
     mach = np.atleast_1d(np.asarray(mach, dtype=np.float64))
@@ -267,12 +300,18 @@ def train(mlp: MLP, feats_dev, targets_dev, epochs=40, batch=8192, lr=2e-3, lr_f
     return losses
 
 
-def predict_state(mlp: MLP, cloud, wall_d, mach, alpha_deg):
+def predict_state(mlp: MLP, cloud, wall_d, mach, alpha_deg, arc=None):
     """Network prediction of the primitive state for one condition (n x 4),
-    or None when it is not physical (the caller keeps the free stream)."""
+    or None when it is not physical (the caller keeps the free stream).
+    With `arc` (wall_arc) the inputs are wall_features, else the library's
+    Fourier encoding."""
     import torch
-    raw = torch.from_numpy(raw_inputs(cloud, wall_d, [mach], [alpha_deg])[0]).cuda()
-    out = mlp.predict(mlp.features(raw)).cpu().numpy()
+    if arc is None:
+        raw = torch.from_numpy(raw_inputs(cloud, wall_d, [mach], [alpha_deg])[0]).cuda()
+        feat = mlp.features(raw)
+    else:
+        feat = torch.from_numpy(wall_features(cloud, wall_d, arc, mach, alpha_deg, mlp.proj)).cuda()
+    out = mlp.predict(feat).cpu().numpy()
     W = state_from_output(out, mach, alpha_deg)
     if not np.all(np.isfinite(W)) or np.any(W[:, 0] <= 0.05) or np.any(W[:, 3] <= 0.05):
         return None

@@ -42,6 +42,9 @@ def main():
     ap.add_argument("--proj-scales", default="1,1,1,1,1,1,1,1",
                     help="standard deviations of the 8 Fourier projections")
     ap.add_argument("--batch", type=int, default=8192)
+    ap.add_argument("--features", default="fourier", choices=["fourier", "wall"],
+                    help="network inputs: the library's Fourier encoding, or wall-loop "
+                         "position harmonics (surrogate.wall_features)")
     ap.add_argument("--data-cache", default="",
                     help="file (.npy) to keep the converged training states in between runs")
     args = ap.parse_args()
@@ -66,7 +69,12 @@ def main():
     T = np.concatenate([S.targets(W_tr[k], m_tr[k], a_tr[k]) for k in range(args.train)])
     scales = [float(v) for v in args.proj_scales.split(",")]
     net = S.MLP(capacity=16384, seed=0, proj=S.projection(scales=scales))
-    feats = net.features(torch.from_numpy(raw).cuda())
+    arc = S.wall_arc(cloud) if args.features == "wall" else None
+    if arc is None:
+        feats = net.features(torch.from_numpy(raw).cuda())
+    else:
+        feats = torch.from_numpy(np.concatenate(
+            [S.wall_features(cloud, wd, arc, m_tr[k], a_tr[k], net.proj) for k in range(args.train)])).cuda()
     Td = torch.from_numpy(T).cuda()
     t0 = time.time()
     losses = S.train(net, feats, Td, epochs=args.epochs, batch=args.batch, lr=2e-3, lr_final=2e-5,
@@ -78,7 +86,7 @@ def main():
     nc = 1 << int(np.ceil(np.log2(n)))
     pred, fallback = [], 0
     for k in range(n):
-        W = S.predict_state(net, cloud, wd, m_te[k], a_te[k])
+        W = S.predict_state(net, cloud, wd, m_te[k], a_te[k], arc=arc)
         if W is None:
             fallback += 1
             W = np.tile(S.freestream(m_te[k], a_te[k]), (cloud.n, 1))
@@ -120,6 +128,7 @@ def main():
     out = {
         "cloud_points": cloud.n, "train_conditions": args.train, "test_conditions": n,
         "eval_cfl": args.eval_cfl, "precision": args.precision, "proj_scales": scales,
+        "features": args.features,
         "epochs": args.epochs,
         "data_seconds": t_data, "train_seconds": t_train,
         "loss_first": losses[0], "loss_last": losses[-1], "fallbacks": fallback,
