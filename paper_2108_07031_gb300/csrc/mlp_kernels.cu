@@ -534,13 +534,11 @@ cudaError_t launch_tc(lskum_mlp* h, dim3 grid, const __nv_bfloat16* A, int64_t s
                       const __nv_bfloat16* B, int64_t sbk, int64_t sbn, int M, int N, int K,
                       const float* bias, float* Cf, __nv_bfloat16* Cb, int64_t ldc, int kchunk) {
     constexpr size_t smem = tc_smem_bytes(AK, BK);
-    static bool attr_set = false;  // the opt-in above 48 KB of dynamic shared memory, once
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_gemm_bf16_tc<EPI, AK, BK>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    // the opt-in above 48 KB of dynamic shared memory (per device, so set on
+    // every launch: a cheap host call next to a GEMM)
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_bf16_tc<EPI, AK, BK>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
     k_gemm_bf16_tc<EPI, AK, BK><<<grid, 256, smem, h->stream>>>(A, sam, sak, B, sbk, sbn, M, N, K, bias,
                                                                 Cf, Cb, ldc, kchunk);
     return cudaGetLastError();
