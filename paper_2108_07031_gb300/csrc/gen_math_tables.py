@@ -91,7 +91,8 @@ def erfcx_pieces_f32():
     return centres, pieces, worst
 
 
-def main():
+def main(path=None):
+    """Writes the header to `path` (default: math_tables.h next to this file)."""
     centres = []
     pieces = []
     worst = 0.0
@@ -117,7 +118,8 @@ def main():
     ln2_64 = mp.log(2) / 64
     hi = float(ln2_64)
     lo = float(ln2_64 - mp.mpf(hi))
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "math_tables.h")
+    if path is None:
+        path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "math_tables.h")
     with open(path, "w") as f:
         f.write("// Generated by gen_math_tables.py -- do not edit.\n")
         f.write("// Chebyshev interpolants (mpmath, 50 digits) of erfcx(a) = exp(a^2) erfc(a)\n")
