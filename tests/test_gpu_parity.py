@@ -149,6 +149,29 @@ def test_1000_iterations_parity(c5k):
     assert abs(cl - cl_o) < 1e-9 and abs(cd - cd_o) < 1e-9
 
 
+def test_converged_solution_parity(c5k):
+    """The steady solution: 12,000 iterations at CFL 0.8 from the free stream
+    (M 0.63, alpha 2 deg; the residue drops 6.7 orders), state, Cl and Cd
+    against the oracle's."""
+    oc = oracle_for(c5k)
+    W0 = np.tile(O.freestream(0.63, 2.0), (c5k.n, 1))
+    W_o, res_o, st = O.iterate(oc, W0, 12000, cfl=0.8)
+    assert st == 0
+    assert res_o[-1] < 1e-6 * res_o[1]
+    cl_o, cd_o = O.forces(oc, W_o, c5k.wall_loop, 0.63, 2.0)
+    with L.Solver.from_cloud(c5k, cfl=0.8) as s:
+        s.set_freestream(0.63, 2.0)
+        s.step(12000)
+        W = s.get_state()
+        r = s.residual_norm()
+        cl, cd = s.forces()
+    print(f"converged: Cl {cl:.12f} vs {cl_o:.12f}, Cd {cd:.12f} vs {cd_o:.12f}, "
+          f"state {normwise(W, W_o):.2e}, residue {r:.3e} vs {res_o[-1]:.3e}")
+    assert normwise(W, W_o) < 1e-9
+    assert abs(cl - cl_o) < 1e-9 and abs(cd - cd_o) < 1e-9
+    assert abs(r - res_o[-1]) < 1e-3 * res_o[-1]
+
+
 @pytest.mark.parametrize("opts", [
     dict(order=1, inner_iters=0),
     dict(inner_iters=0),
