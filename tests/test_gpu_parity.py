@@ -152,7 +152,7 @@ def test_1000_iterations_parity(c5k):
 def test_converged_solution_parity(c5k):
     """The steady solution: 12,000 iterations at CFL 0.8 from the free stream
     (M 0.63, alpha 2 deg; the residue drops 6.7 orders), state, Cl and Cd
-    against the oracle's."""
+    against the oracle's -- the FP64 path to 1e-9, the mixed path to 1e-4."""
     oc = oracle_for(c5k)
     W0 = np.tile(O.freestream(0.63, 2.0), (c5k.n, 1))
     W_o, res_o, st = O.iterate(oc, W0, 12000, cfl=0.8)
@@ -170,6 +170,16 @@ def test_converged_solution_parity(c5k):
     assert normwise(W, W_o) < 1e-9
     assert abs(cl - cl_o) < 1e-9 and abs(cd - cd_o) < 1e-9
     assert abs(r - res_o[-1]) < 1e-3 * res_o[-1]
+    # the mixed-precision path reaches the same steady state to its bar
+    # (Cl and Cd within 1e-4 of FP64)
+    with L.Solver.from_cloud(c5k, cfl=0.8, precision=L.MIXED) as s:
+        s.set_freestream(0.63, 2.0)
+        s.step(12000)
+        Wm = s.get_state()
+        clm, cdm = s.forces()
+    print(f"mixed converged: Cl {clm:.9f}, Cd {cdm:.9f}, state {normwise(Wm, W_o):.2e}")
+    assert abs(clm - cl_o) < 1e-4 and abs(cdm - cd_o) < 1e-4
+    assert normwise(Wm, W_o) < 1e-4
 
 
 @pytest.mark.parametrize("opts", [
