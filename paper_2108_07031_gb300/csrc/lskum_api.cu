@@ -357,13 +357,16 @@ int lskum_create(int64_t n, const double* xy, const double* normals, const int8_
     } else {
         // FP32 records per neighbour entry: {wx, wy, hdx, hdy} and {ws, wn, hdx, hdy}
         std::vector<float4> lsw(L.wx.size()), fxw(L.wx.size());
+        std::vector<float2> lw2(L.wx.size());
         for (size_t i = 0; i < lsw.size(); ++i) {
             const float hx = float(L.hdx[i]), hy = float(L.hdy[i]);
             lsw[i] = make_float4(float(L.wx[i]), float(L.wy[i]), hx, hy);
             fxw[i] = make_float4(float(L.ws[i]), float(L.wn[i]), hx, hy);
+            lw2[i] = make_float2(lsw[i].x, lsw[i].y);
         }
         if ((e = upload(c, &c->g32.lsw, lsw)) != cudaSuccess ||
-            (e = upload(c, &c->g32.fxw, fxw)) != cudaSuccess)
+            (e = upload(c, &c->g32.fxw, fxw)) != cudaSuccess ||
+            (e = upload(c, &c->g32.lw2, lw2)) != cudaSuccess)
             return bail(e, "upload of the FP32 cloud layout");
     }
 

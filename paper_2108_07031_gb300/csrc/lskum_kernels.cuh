@@ -37,6 +37,7 @@ struct DevGeom32 {
     // kernel fetches its per-neighbour constants with one vector load
     const float4* lsw;  // {wx, wy, hdx, hdy}: least-squares weights (Eq. 11), half offsets
     const float4* fxw;  // {ws, wn, hdx, hdy}: split-stencil weights (Eq. 24), half offsets
+    const float2* lw2;  // {wx, wy} alone, for the first-order sweep
 };
 
 // Static cloud data on the device (device point order).

@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(BLOCK) k_ls_first_mx(const DevGeom g, const De
     for (int k = 0; k < c; ++k) {
         const int64_t at = int64_t(k) * g.stride + d;
         const uint32_t j = g.nbr[at] & kIndexMask;
-        const float4 lw = g32.lsw[at];
+        const float2 lw = g32.lw2[at];
         const float wx = lw.x, wy = lw.y;
         const float4 dqv = qdiff(q[sidx(g, j, cc)], qi);
         ax.x += wx * dqv.x; ax.y += wx * dqv.y; ax.z += wx * dqv.z; ax.w += wx * dqv.w;
