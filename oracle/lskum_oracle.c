@@ -64,14 +64,49 @@
  * Compiled with -O2 -ffp-contract=off (no fused multiply-add contraction) and
  * optional OpenMP over points (each point's outputs are written by one
  * thread; reductions are serial, so results do not depend on thread count).
+ *
+ * Precision. The arithmetic is written once, on the type `real`: double by
+ * default (the FP64 oracle), IEEE binary128 (_Float128, a 113-bit significand,
+ * libm's *f128 functions) when compiled with -DORC_QUAD. The binary128 build
+ * evaluates the same formulas in the same order on the same double inputs
+ * (coordinates, normals, states, gamma), converted exactly; it is the
+ * extended-precision reference that measures how far an FP64 evaluation of
+ * the method lies from the exact result of its formulas. Arrays of `real`
+ * cross the library boundary as opaque buffers of orc_real_bytes() bytes per
+ * value, filled and read with orc_to_real / orc_from_real (value = hi + lo).
  */
 
+#ifdef ORC_QUAD
+#define __STDC_WANT_IEC_60559_TYPES_EXT__ 1
+#endif
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 
-#define ORC_PI 3.14159265358979323846
+#ifdef ORC_QUAD
+typedef _Float128 real;
+#define R_LIT(v) v##F128
+#define R_EXP expf128
+#define R_LOG logf128
+#define R_ERFC erfcf128
+#define R_SQRT sqrtf128
+#define R_POW powf128
+#define R_SIN sinf128
+#define R_COS cosf128
+#else
+typedef double real;
+#define R_LIT(v) v
+#define R_EXP exp
+#define R_LOG log
+#define R_ERFC erfc
+#define R_SQRT sqrt
+#define R_POW pow
+#define R_SIN sin
+#define R_COS cos
+#endif
+
+#define ORC_PI R_LIT(3.14159265358979323846264338327950288)
 
 enum { ORC_INTERIOR = 0, ORC_WALL = 1, ORC_OUTER = 2 };
 
@@ -91,58 +126,82 @@ typedef struct {
     double weight_power; /* least-squares weight |P_j - P_i|^-weight_power; 0: unweighted */
 } orc_cloud;
 
+/* ------------------------------------------------------------ real buffers */
+
+/* Bytes of one `real` value (8 in the FP64 build, 16 in the binary128 build). */
+int orc_real_bytes(void) { return (int)sizeof(real); }
+
+/* out[i] = hi[i] + lo[i] (lo may be NULL), rounded to `real`. */
+void orc_to_real(int64_t n, const double* hi, const double* lo, real* out) {
+    for (int64_t i = 0; i < n; ++i) out[i] = lo ? (real)hi[i] + (real)lo[i] : (real)hi[i];
+}
+
+/* hi[i] = in[i] rounded to double; lo[i] (lo may be NULL) = the remainder,
+ * rounded to double. */
+void orc_from_real(int64_t n, const real* in, double* hi, double* lo) {
+    for (int64_t i = 0; i < n; ++i) {
+        double h = (double)in[i];
+        hi[i] = h;
+        if (lo) lo[i] = (double)(in[i] - (real)h);
+    }
+}
+
+/* Offset P_j - P_i of neighbour j seen from point i (exact in binary128). */
+static real offset_x(const orc_cloud* c, int64_t i, int64_t j) { return (real)c->x[j] - (real)c->x[i]; }
+static real offset_y(const orc_cloud* c, int64_t i, int64_t j) { return (real)c->y[j] - (real)c->y[i]; }
+
 /* Weight of neighbour offset (dx, dy) in the least-squares sums. */
-static double ls_weight(const orc_cloud* c, double dx, double dy) {
-    if (c->weight_power == 0.0) return 1.0;
-    return pow(dx * dx + dy * dy, -0.5 * c->weight_power);
+static real ls_weight(const orc_cloud* c, real dx, real dy) {
+    if (c->weight_power == 0.0) return 1;
+    return R_POW(dx * dx + dy * dy, (real)-0.5 * (real)c->weight_power);
 }
 
 /* ---------------------------------------------------------------- state maps */
 
 /* Eqs. 2-3: conserved U = (rho, rho u1, rho u2, rho e) from W = (rho, u1, u2, p). */
-void orc_prim_to_cons(const double* W, double gamma, double* U) {
-    double rho = W[0], u1 = W[1], u2 = W[2], p = W[3];
+void orc_prim_to_cons(const real* W, double gamma, real* U) {
+    real rho = W[0], u1 = W[1], u2 = W[2], p = W[3];
     U[0] = rho;
     U[1] = rho * u1;
     U[2] = rho * u2;
-    U[3] = p / (gamma - 1.0) + 0.5 * rho * (u1 * u1 + u2 * u2);
+    U[3] = p / ((real)gamma - 1) + (real)0.5 * rho * (u1 * u1 + u2 * u2);
 }
 
-void orc_cons_to_prim(const double* U, double gamma, double* W) {
-    double rho = U[0];
-    double u1 = U[1] / rho, u2 = U[2] / rho;
+void orc_cons_to_prim(const real* U, double gamma, real* W) {
+    real rho = U[0];
+    real u1 = U[1] / rho, u2 = U[2] / rho;
     W[0] = rho;
     W[1] = u1;
     W[2] = u2;
-    W[3] = (gamma - 1.0) * (U[3] - 0.5 * rho * (u1 * u1 + u2 * u2));
+    W[3] = ((real)gamma - 1) * (U[3] - (real)0.5 * rho * (u1 * u1 + u2 * u2));
 }
 
 /* Eq. 26: q = (ln rho + ln beta/(gamma-1) - beta |u|^2, 2 beta u1, 2 beta u2, -2 beta),
  * beta = 1/(2RT) = rho/(2p). */
-void orc_prim_to_q(const double* W, double gamma, double* q) {
-    double rho = W[0], u1 = W[1], u2 = W[2], p = W[3];
-    double beta = rho / (2.0 * p);
-    q[0] = log(rho) + log(beta) / (gamma - 1.0) - beta * (u1 * u1 + u2 * u2);
-    q[1] = 2.0 * beta * u1;
-    q[2] = 2.0 * beta * u2;
-    q[3] = -2.0 * beta;
+void orc_prim_to_q(const real* W, double gamma, real* q) {
+    real rho = W[0], u1 = W[1], u2 = W[2], p = W[3];
+    real beta = rho / (2 * p);
+    q[0] = R_LOG(rho) + R_LOG(beta) / ((real)gamma - 1) - beta * (u1 * u1 + u2 * u2);
+    q[1] = 2 * beta * u1;
+    q[2] = 2 * beta * u2;
+    q[3] = -2 * beta;
 }
 
 /* Inverse of Eq. 26 (the map U <-> q is one to one, Section 2.1). Returns 0,
  * or 1 when q4 >= 0 (no positive temperature). */
-int orc_q_to_prim(const double* q, double gamma, double* W) {
-    double beta = -0.5 * q[3];
-    if (!(beta > 0.0)) {
+int orc_q_to_prim(const real* q, double gamma, real* W) {
+    real beta = (real)-0.5 * q[3];
+    if (!(beta > 0)) {
         W[0] = W[1] = W[2] = W[3] = NAN;
         return 1;
     }
-    double u1 = q[1] / (2.0 * beta);
-    double u2 = q[2] / (2.0 * beta);
-    double rho = exp(q[0] - log(beta) / (gamma - 1.0) + beta * (u1 * u1 + u2 * u2));
+    real u1 = q[1] / (2 * beta);
+    real u2 = q[2] / (2 * beta);
+    real rho = R_EXP(q[0] - R_LOG(beta) / ((real)gamma - 1) + beta * (u1 * u1 + u2 * u2));
     W[0] = rho;
     W[1] = u1;
     W[2] = u2;
-    W[3] = rho / (2.0 * beta);
+    W[3] = rho / (2 * beta);
     return 0;
 }
 
@@ -153,20 +212,20 @@ int orc_q_to_prim(const double* q, double gamma, double* W) {
  * the components of W's frame (mass, momentum 1, momentum 2, energy).
  * Half-range moments of the Maxwellian of Eq. 5 over v_dir > 0 (sign = +1) or
  * v_dir < 0 (sign = -1), the CIR split of Eqs. 8-9. */
-void orc_split_flux(const double* W, int dir, int sign, double gamma, double* G) {
-    double rho = W[0], p = W[3];
-    double ua = dir == 0 ? W[1] : W[2];
-    double ub = dir == 0 ? W[2] : W[1];
-    double beta = rho / (2.0 * p);
-    double S = ua * sqrt(beta);
-    double sg = sign > 0 ? 1.0 : -1.0;
-    double A = 0.5 * erfc(-sg * S);
-    double B = exp(-S * S) / (2.0 * sqrt(ORC_PI * beta));
-    double rhoe = p / (gamma - 1.0) + 0.5 * rho * (ua * ua + ub * ub);
-    double g_mass = rho * (ua * A + sg * B);
-    double g_a = (p + rho * ua * ua) * A + sg * rho * ua * B;
-    double g_b = rho * ub * (ua * A + sg * B);
-    double g_e = (p + rhoe) * ua * A + sg * (rhoe + 0.5 * p) * B;
+void orc_split_flux(const real* W, int dir, int sign, double gamma, real* G) {
+    real rho = W[0], p = W[3];
+    real ua = dir == 0 ? W[1] : W[2];
+    real ub = dir == 0 ? W[2] : W[1];
+    real beta = rho / (2 * p);
+    real S = ua * R_SQRT(beta);
+    real sg = sign > 0 ? 1 : -1;
+    real A = (real)0.5 * R_ERFC(-sg * S);
+    real B = R_EXP(-S * S) / (2 * R_SQRT(ORC_PI * beta));
+    real rhoe = p / ((real)gamma - 1) + (real)0.5 * rho * (ua * ua + ub * ub);
+    real g_mass = rho * (ua * A + sg * B);
+    real g_a = (p + rho * ua * ua) * A + sg * rho * ua * B;
+    real g_b = rho * ub * (ua * A + sg * B);
+    real g_e = (p + rhoe) * ua * A + sg * (rhoe + (real)0.5 * p) * B;
     G[0] = g_mass;
     G[1] = dir == 0 ? g_a : g_b;
     G[2] = dir == 0 ? g_b : g_a;
@@ -174,23 +233,23 @@ void orc_split_flux(const double* W, int dir, int sign, double gamma, double* G)
 }
 
 /* Array forms of the point maps (n rows of 4). */
-void orc_prim_to_q_n(int64_t n, const double* W, double gamma, double* q) {
+void orc_prim_to_q_n(int64_t n, const real* W, double gamma, real* q) {
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) orc_prim_to_q(W + 4 * i, gamma, q + 4 * i);
 }
-void orc_q_to_prim_n(int64_t n, const double* q, double gamma, double* W) {
+void orc_q_to_prim_n(int64_t n, const real* q, double gamma, real* W) {
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) orc_q_to_prim(q + 4 * i, gamma, W + 4 * i);
 }
-void orc_prim_to_cons_n(int64_t n, const double* W, double gamma, double* U) {
+void orc_prim_to_cons_n(int64_t n, const real* W, double gamma, real* U) {
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) orc_prim_to_cons(W + 4 * i, gamma, U + 4 * i);
 }
-void orc_cons_to_prim_n(int64_t n, const double* U, double gamma, double* W) {
+void orc_cons_to_prim_n(int64_t n, const real* U, double gamma, real* W) {
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) orc_cons_to_prim(U + 4 * i, gamma, W + 4 * i);
 }
-void orc_split_flux_n(int64_t n, const double* W, int dir, int sign, double gamma, double* G) {
+void orc_split_flux_n(int64_t n, const real* W, int dir, int sign, double gamma, real* G) {
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) orc_split_flux(W + 4 * i, dir, sign, gamma, G + 4 * i);
 }
@@ -201,34 +260,34 @@ void orc_split_flux_n(int64_t n, const double* W, int dir, int sign, double gamm
  * NULL it is the first-order formula of Eq. 11 applied to q; otherwise it is
  * Eq. 29 with the perturbations dq~ = q~_j - q~_0 of Eq. 28 built from the
  * previous derivative iterate (px, py). q, px, py, qx, qy are n x 4. */
-void orc_ls_sweep(const orc_cloud* c, const double* q, const double* px, const double* py,
-                  double* qx, double* qy) {
+void orc_ls_sweep(const orc_cloud* c, const real* q, const real* px, const real* py,
+                  real* qx, real* qy) {
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < c->n; ++i) {
-        double sxx = 0, sxy = 0, syy = 0;
-        double sxq[4] = {0, 0, 0, 0}, syq[4] = {0, 0, 0, 0};
+        real sxx = 0, sxy = 0, syy = 0;
+        real sxq[4] = {0, 0, 0, 0}, syq[4] = {0, 0, 0, 0};
         for (int32_t e = c->off[i]; e < c->off[i + 1]; ++e) {
             int32_t j = c->nbr[e];
-            double dx = c->x[j] - c->x[i];
-            double dy = c->y[j] - c->y[i];
-            double w = ls_weight(c, dx, dy);
+            real dx = offset_x(c, i, j);
+            real dy = offset_y(c, i, j);
+            real w = ls_weight(c, dx, dy);
             sxx += w * dx * dx;
             sxy += w * dx * dy;
             syy += w * dy * dy;
             for (int m = 0; m < 4; ++m) {
-                double dq;
+                real dq;
                 if (px == NULL) {
                     dq = q[4 * j + m] - q[4 * i + m];
                 } else {
-                    double qtj = q[4 * j + m] - 0.5 * (dx * px[4 * j + m] + dy * py[4 * j + m]);
-                    double qt0 = q[4 * i + m] - 0.5 * (dx * px[4 * i + m] + dy * py[4 * i + m]);
+                    real qtj = q[4 * j + m] - (real)0.5 * (dx * px[4 * j + m] + dy * py[4 * j + m]);
+                    real qt0 = q[4 * i + m] - (real)0.5 * (dx * px[4 * i + m] + dy * py[4 * i + m]);
                     dq = qtj - qt0;
                 }
                 sxq[m] += w * dx * dq;
                 syq[m] += w * dy * dq;
             }
         }
-        double det = sxx * syy - sxy * sxy;
+        real det = sxx * syy - sxy * sxy;
         for (int m = 0; m < 4; ++m) {
             qx[4 * i + m] = (sxq[m] * syy - sxy * syq[m]) / det;
             qy[4 * i + m] = (sxx * syq[m] - sxy * sxq[m]) / det;
@@ -239,10 +298,10 @@ void orc_ls_sweep(const orc_cloud* c, const double* q, const double* px, const d
 /* q_derivatives(): the first-order sweep, then `inner` Jacobi sweeps of the
  * implicit defect-corrected formula (Eqs. 28-29), each using only the
  * previous sweep's derivatives. */
-void orc_q_derivatives(const orc_cloud* c, const double* q, int inner, double* qx, double* qy) {
-    size_t sz = sizeof(double) * 4 * (size_t)c->n;
-    double* px = (double*)malloc(sz);
-    double* py = (double*)malloc(sz);
+void orc_q_derivatives(const orc_cloud* c, const real* q, int inner, real* qx, real* qy) {
+    size_t sz = sizeof(real) * 4 * (size_t)c->n;
+    real* px = (real*)malloc(sz);
+    real* py = (real*)malloc(sz);
     orc_ls_sweep(c, q, NULL, NULL, qx, qy);
     for (int sweep = 1; sweep <= inner; ++sweep) {
         memcpy(px, qx, sz);
@@ -255,12 +314,12 @@ void orc_q_derivatives(const orc_cloud* c, const double* q, int inner, double* q
 
 /* ------------------------------------------------------------ flux residual */
 
-static void frame_of(const orc_cloud* c, int64_t i, double* tx, double* ty, double* nx, double* ny) {
+static void frame_of(const orc_cloud* c, int64_t i, real* tx, real* ty, real* nx, real* ny) {
     if (c->flag[i] == ORC_INTERIOR) {
-        *tx = 1.0; *ty = 0.0; *nx = 0.0; *ny = 1.0;
+        *tx = 1; *ty = 0; *nx = 0; *ny = 1;
     } else {
         *nx = c->nx[i]; *ny = c->ny[i];
-        *tx = c->ny[i]; *ty = -c->nx[i];
+        *tx = c->ny[i]; *ty = -(real)c->nx[i];
     }
 }
 
@@ -270,35 +329,35 @@ static void frame_of(const orc_cloud* c, int64_t i, double* tx, double* ty, doub
  * components in the global frame; dU/dt + R = 0. Returns the number of
  * split stencils whose determinant was not positive (their derivative is
  * taken as 0). */
-static int residual_point(const orc_cloud* c, int64_t i, const double* q, const double* qx,
-                          const double* qy, double* R) {
+static int residual_point(const orc_cloud* c, int64_t i, const real* q, const real* qx,
+                          const real* qy, real* R) {
     if (c->outer_mode == 1 && c->flag[i] == ORC_OUTER) {
         /* far-field points held at the free stream are not unknowns */
-        R[0] = R[1] = R[2] = R[3] = 0.0;
+        R[0] = R[1] = R[2] = R[3] = 0;
         return 0;
     }
-    double tx, ty, nx, ny;
+    real tx, ty, nx, ny;
     frame_of(c, i, &tx, &ty, &nx, &ny);
     int flag = c->flag[i];
     /* stencil slots: 0 s+ (ds<0), 1 s- (ds>0), 2 n+ (dn<0), 3 n- (dn>0) */
     int use[4] = {1, 1, flag != ORC_WALL, flag != ORC_OUTER};
-    double sss[4] = {0}, ssn[4] = {0}, snn[4] = {0};
-    double sdg_s[4][4] = {{0}}, sdg_n[4][4] = {{0}};
+    real sss[4] = {0}, ssn[4] = {0}, snn[4] = {0};
+    real sdg_s[4][4] = {{0}}, sdg_n[4][4] = {{0}};
     double gamma = c->gamma;
     for (int32_t e = c->off[i]; e < c->off[i + 1]; ++e) {
         int32_t j = c->nbr[e];
-        double dx = c->x[j] - c->x[i];
-        double dy = c->y[j] - c->y[i];
-        double ds = dx * tx + dy * ty;
-        double dn = dx * nx + dy * ny;
-        double qtj[4], qt0[4], Wj[4], W0[4], Lj[4], L0[4];
+        real dx = offset_x(c, i, j);
+        real dy = offset_y(c, i, j);
+        real ds = dx * tx + dy * ty;
+        real dn = dx * nx + dy * ny;
+        real qtj[4], qt0[4], Wj[4], W0[4], Lj[4], L0[4];
         for (int m = 0; m < 4; ++m) {
             if (c->order == 1) {
                 qtj[m] = q[4 * j + m];
                 qt0[m] = q[4 * i + m];
             } else {
-                qtj[m] = q[4 * j + m] - 0.5 * (dx * qx[4 * j + m] + dy * qy[4 * j + m]);
-                qt0[m] = q[4 * i + m] - 0.5 * (dx * qx[4 * i + m] + dy * qy[4 * i + m]);
+                qtj[m] = q[4 * j + m] - (real)0.5 * (dx * qx[4 * j + m] + dy * qy[4 * j + m]);
+                qt0[m] = q[4 * i + m] - (real)0.5 * (dx * qx[4 * i + m] + dy * qy[4 * i + m]);
             }
         }
         orc_q_to_prim(qtj, gamma, Wj);
@@ -306,41 +365,41 @@ static int residual_point(const orc_cloud* c, int64_t i, const double* q, const 
         /* velocities into the local frame: (rho, u_s, u_n, p) */
         Lj[0] = Wj[0]; Lj[1] = Wj[1] * tx + Wj[2] * ty; Lj[2] = Wj[1] * nx + Wj[2] * ny; Lj[3] = Wj[3];
         L0[0] = W0[0]; L0[1] = W0[1] * tx + W0[2] * ty; L0[2] = W0[1] * nx + W0[2] * ny; L0[3] = W0[3];
-        int slot_s = ds < 0.0 ? 0 : (ds > 0.0 ? 1 : -1);
-        int slot_n = dn < 0.0 ? 2 : (dn > 0.0 ? 3 : -1);
+        int slot_s = ds < 0 ? 0 : (ds > 0 ? 1 : -1);
+        int slot_n = dn < 0 ? 2 : (dn > 0 ? 3 : -1);
         int slots[2] = {slot_s, slot_n};
         for (int k = 0; k < 2; ++k) {
             int sl = slots[k];
             if (sl < 0 || !use[sl]) continue;
             int dir = sl < 2 ? 0 : 1;
             int sign = (sl == 0 || sl == 2) ? 1 : -1;
-            double Gj[4], G0[4];
+            real Gj[4], G0[4];
             orc_split_flux(Lj, dir, sign, gamma, Gj);
             orc_split_flux(L0, dir, sign, gamma, G0);
-            double w = ls_weight(c, dx, dy);
+            real w = ls_weight(c, dx, dy);
             sss[sl] += w * ds * ds;
             ssn[sl] += w * ds * dn;
             snn[sl] += w * dn * dn;
             for (int m = 0; m < 4; ++m) {
-                double dG = Gj[m] - G0[m];
+                real dG = Gj[m] - G0[m];
                 sdg_s[sl][m] += w * ds * dG;
                 sdg_n[sl][m] += w * dn * dG;
             }
         }
     }
     int bad = 0;
-    double Rl[4] = {0, 0, 0, 0};
+    real Rl[4] = {0, 0, 0, 0};
     for (int sl = 0; sl < 4; ++sl) {
         if (!use[sl]) continue;
-        double det = sss[sl] * snn[sl] - ssn[sl] * ssn[sl];
-        if (!(det > 0.0)) { ++bad; continue; }
+        real det = sss[sl] * snn[sl] - ssn[sl] * ssn[sl];
+        if (!(det > 0)) { ++bad; continue; }
         for (int m = 0; m < 4; ++m) {
-            double d;
+            real d;
             if (sl < 2) /* d/ds: Cramer's rule, first unknown */
                 d = (sdg_s[sl][m] * snn[sl] - ssn[sl] * sdg_n[sl][m]) / det;
             else        /* d/dn: second unknown */
                 d = (sss[sl] * sdg_n[sl][m] - ssn[sl] * sdg_s[sl][m]) / det;
-            if (sl == 3 && flag == ORC_WALL) d = c->wall_factor * d;
+            if (sl == 3 && flag == ORC_WALL) d = (real)c->wall_factor * d;
             Rl[m] += d;
         }
     }
@@ -351,8 +410,8 @@ static int residual_point(const orc_cloud* c, int64_t i, const double* q, const 
     return bad;
 }
 
-int orc_flux_residual(const orc_cloud* c, const double* q, const double* qx, const double* qy,
-                      double* R) {
+int orc_flux_residual(const orc_cloud* c, const real* q, const real* qx, const real* qy,
+                      real* R) {
     int bad = 0;
 #pragma omp parallel for schedule(static) reduction(+ : bad)
     for (int64_t i = 0; i < c->n; ++i) bad += residual_point(c, i, q, qx, qy, R + 4 * i);
@@ -360,8 +419,8 @@ int orc_flux_residual(const orc_cloud* c, const double* q, const double* qx, con
 }
 
 /* Residual at a subset of points only (for sampled checks on large clouds). */
-int orc_flux_residual_subset(const orc_cloud* c, const double* q, const double* qx,
-                             const double* qy, const int64_t* idx, int64_t m, double* R) {
+int orc_flux_residual_subset(const orc_cloud* c, const real* q, const real* qx,
+                             const real* qy, const int64_t* idx, int64_t m, real* R) {
     int bad = 0;
 #pragma omp parallel for schedule(static) reduction(+ : bad)
     for (int64_t k = 0; k < m; ++k) bad += residual_point(c, idx[k], q, qx, qy, R + 4 * k);
@@ -371,20 +430,20 @@ int orc_flux_residual_subset(const orc_cloud* c, const double* q, const double* 
 /* --------------------------------------------------------- time step, RK */
 
 /* Local time step dt_i = CFL min_j d_ij / (|u_i| + a_i), a = sqrt(gamma p / rho). */
-void orc_timestep(const orc_cloud* c, const double* W, double cfl, double* dt) {
+void orc_timestep(const orc_cloud* c, const real* W, double cfl, real* dt) {
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < c->n; ++i) {
-        double dmin = INFINITY;
+        real dmin = INFINITY;
         for (int32_t e = c->off[i]; e < c->off[i + 1]; ++e) {
             int32_t j = c->nbr[e];
-            double dx = c->x[j] - c->x[i];
-            double dy = c->y[j] - c->y[i];
-            double d = sqrt(dx * dx + dy * dy);
+            real dx = offset_x(c, i, j);
+            real dy = offset_y(c, i, j);
+            real d = R_SQRT(dx * dx + dy * dy);
             if (d < dmin) dmin = d;
         }
-        const double* w = W + 4 * i;
-        double speed = sqrt(w[1] * w[1] + w[2] * w[2]) + sqrt(c->gamma * w[3] / w[0]);
-        dt[i] = cfl * dmin / speed;
+        const real* w = W + 4 * i;
+        real speed = R_SQRT(w[1] * w[1] + w[2] * w[2]) + R_SQRT((real)c->gamma * w[3] / w[0]);
+        dt[i] = (real)cfl * dmin / speed;
     }
 }
 
@@ -394,63 +453,63 @@ void orc_timestep(const orc_cloud* c, const double* W, double cfl, double* dt) {
  *   stage 2: U2 = U1 - dt/2 R(U1)
  *   stage 3: U3 = 2/3 U0 + 1/3 (U2 - dt/2 R(U2))
  *   stage 4: U4 = U3 - dt/2 R(U3)                                          */
-void orc_rk_stage(int stage, const double* U0, const double* U, const double* R, double dt,
-                  double* Unew) {
+void orc_rk_stage(int stage, const real* U0, const real* U, const real* R, real dt,
+                  real* Unew) {
     for (int m = 0; m < 4; ++m) {
         if (stage == 3)
-            Unew[m] = (2.0 / 3.0) * U0[m] + (1.0 / 3.0) * (U[m] - 0.5 * dt * R[m]);
+            Unew[m] = ((real)2 / 3) * U0[m] + ((real)1 / 3) * (U[m] - (real)0.5 * dt * R[m]);
         else
-            Unew[m] = U[m] - 0.5 * dt * R[m];
+            Unew[m] = U[m] - (real)0.5 * dt * R[m];
     }
 }
 
 /* Wall condition on the state: keep rho, the tangential momentum and rho e;
  * the momentum normal to the wall is set to zero. */
-void orc_wall_project(double* U, double nx, double ny) {
-    double tx = ny, ty = -nx;
-    double ms = U[1] * tx + U[2] * ty;
+void orc_wall_project(real* U, double nx, double ny) {
+    real tx = ny, ty = -(real)nx;
+    real ms = U[1] * tx + U[2] * ty;
     U[1] = ms * tx;
     U[2] = ms * ty;
 }
 
 /* residue = sqrt(sum_i R_rho,i^2) / N (serial sum in point order). */
-double orc_residue(int64_t n, const double* R) {
-    double s = 0.0;
+real orc_residue(int64_t n, const real* R) {
+    real s = 0;
     for (int64_t i = 0; i < n; ++i) s += R[4 * i] * R[4 * i];
-    return sqrt(s) / (double)n;
+    return R_SQRT(s) / (real)n;
 }
 
 /* Pressure force on the wall loop and the lift/drag coefficients. The loop
  * lists the wall points in order (closed: the last connects to the first). */
-void orc_forces(const orc_cloud* c, const double* W, const int64_t* loop, int64_t m,
-                double mach, double alpha_deg, double* cl, double* cd) {
-    double p_inf = 1.0 / c->gamma;
-    double fx = 0.0, fy = 0.0;
+void orc_forces(const orc_cloud* c, const real* W, const int64_t* loop, int64_t m,
+                double mach, double alpha_deg, real* cl, real* cd) {
+    real p_inf = 1 / (real)c->gamma;
+    real fx = 0, fy = 0;
     for (int64_t k = 0; k < m; ++k) {
         int64_t i = loop[k];
         int64_t ip = loop[(k + 1) % m];
         int64_t im = loop[(k + m - 1) % m];
-        double lp = sqrt((c->x[ip] - c->x[i]) * (c->x[ip] - c->x[i]) +
-                         (c->y[ip] - c->y[i]) * (c->y[ip] - c->y[i]));
-        double lm = sqrt((c->x[i] - c->x[im]) * (c->x[i] - c->x[im]) +
-                         (c->y[i] - c->y[im]) * (c->y[i] - c->y[im]));
-        double ds = 0.5 * (lp + lm);
-        double dp = W[4 * i + 3] - p_inf;
-        fx -= dp * c->nx[i] * ds;
-        fy -= dp * c->ny[i] * ds;
+        real next_x = offset_x(c, i, ip), next_y = offset_y(c, i, ip);
+        real prev_x = offset_x(c, im, i), prev_y = offset_y(c, im, i);
+        real lp = R_SQRT(next_x * next_x + next_y * next_y);
+        real lm = R_SQRT(prev_x * prev_x + prev_y * prev_y);
+        real ds = (real)0.5 * (lp + lm);
+        real dp = W[4 * i + 3] - p_inf;
+        fx -= dp * (real)c->nx[i] * ds;
+        fy -= dp * (real)c->ny[i] * ds;
     }
-    double a = alpha_deg * ORC_PI / 180.0;
-    double qinf = 0.5 * mach * mach;
-    *cl = (-fx * sin(a) + fy * cos(a)) / qinf;
-    *cd = (fx * cos(a) + fy * sin(a)) / qinf;
+    real a = (real)alpha_deg * ORC_PI / 180;
+    real qinf = (real)0.5 * (real)mach * (real)mach;
+    *cl = (-fx * R_SIN(a) + fy * R_COS(a)) / qinf;
+    *cd = (fx * R_COS(a) + fy * R_SIN(a)) / qinf;
 }
 
-void orc_freestream(double gamma, double mach, double alpha_deg, double* W) {
-    double a = alpha_deg * ORC_PI / 180.0;
-    W[0] = 1.0;
-    W[1] = mach * cos(a);
-    W[2] = mach * sin(a);
-    W[3] = 1.0 / gamma;
+void orc_freestream(double gamma, double mach, double alpha_deg, real* W) {
+    real a = (real)alpha_deg * ORC_PI / 180;
+    W[0] = 1;
+    W[1] = (real)mach * R_COS(a);
+    W[2] = (real)mach * R_SIN(a);
+    W[3] = 1 / (real)gamma;
 }
 
 /* --------------------------------------------------------------- solver */
@@ -462,24 +521,24 @@ void orc_freestream(double gamma, double mach, double alpha_deg, double* W) {
  * stage-1 residual of the last iteration. Returns 0, or the iteration number
  * (1-based) at which a non-positive density/pressure or a non-finite value
  * appeared. */
-int orc_iterate(const orc_cloud* c, double* W, int iters, double cfl, int inner, double* res,
-                double* R1) {
+int orc_iterate(const orc_cloud* c, real* W, int iters, double cfl, int inner, real* res,
+                real* R1) {
     int64_t n = c->n;
     double gamma = c->gamma;
-    size_t sz = sizeof(double) * 4 * (size_t)n;
-    double* U0 = (double*)malloc(sz);
-    double* U = (double*)malloc(sz);
-    double* q = (double*)malloc(sz);
-    double* qx = (double*)malloc(sz);
-    double* qy = (double*)malloc(sz);
-    double* R = (double*)malloc(sz);
-    double* dt = (double*)malloc(sizeof(double) * (size_t)n);
+    size_t sz = sizeof(real) * 4 * (size_t)n;
+    real* U0 = (real*)malloc(sz);
+    real* U = (real*)malloc(sz);
+    real* q = (real*)malloc(sz);
+    real* qx = (real*)malloc(sz);
+    real* qy = (real*)malloc(sz);
+    real* R = (real*)malloc(sz);
+    real* dt = (real*)malloc(sizeof(real) * (size_t)n);
     int status = 0;
     for (int it = 0; it < iters && status == 0; ++it) {
         orc_timestep(c, W, cfl, dt);
         for (int64_t i = 0; i < n; ++i) orc_prim_to_cons(W + 4 * i, gamma, U0 + 4 * i);
         memcpy(U, U0, sz);
-        double r = 0.0;
+        real r = 0;
         for (int stage = 1; stage <= 4; ++stage) {
             for (int64_t i = 0; i < n; ++i) orc_prim_to_q(W + 4 * i, gamma, q + 4 * i);
             orc_q_derivatives(c, q, inner, qx, qy);
@@ -489,14 +548,14 @@ int orc_iterate(const orc_cloud* c, double* W, int iters, double cfl, int inner,
                 if (R1 && it == iters - 1) memcpy(R1, R, sz);
             }
             for (int64_t i = 0; i < n; ++i) {
-                double un[4];
+                real un[4];
                 if (c->outer_mode == 1 && c->flag[i] == ORC_OUTER) continue;
                 orc_rk_stage(stage, U0 + 4 * i, U + 4 * i, R + 4 * i, dt[i], un);
                 if (c->flag[i] == ORC_WALL) orc_wall_project(un, c->nx[i], c->ny[i]);
                 memcpy(U + 4 * i, un, sizeof(un));
                 orc_cons_to_prim(un, gamma, W + 4 * i);
-                const double* w = W + 4 * i;
-                if (!(w[0] > 0.0) || !(w[3] > 0.0) || !isfinite(w[1]) || !isfinite(w[2]))
+                const real* w = W + 4 * i;
+                if (!(w[0] > 0) || !(w[3] > 0) || !isfinite(w[1]) || !isfinite(w[2]))
                     status = it + 1;
             }
         }
@@ -509,12 +568,12 @@ int orc_iterate(const orc_cloud* c, double* W, int iters, double cfl, int inner,
 
 /* R(W): the stage-1 residual of the state W (q_variables, q_derivatives,
  * flux_residual) without updating it. */
-int orc_residual_of_state(const orc_cloud* c, const double* W, int inner, double* R) {
+int orc_residual_of_state(const orc_cloud* c, const real* W, int inner, real* R) {
     int64_t n = c->n;
-    size_t sz = sizeof(double) * 4 * (size_t)n;
-    double* q = (double*)malloc(sz);
-    double* qx = (double*)malloc(sz);
-    double* qy = (double*)malloc(sz);
+    size_t sz = sizeof(real) * 4 * (size_t)n;
+    real* q = (real*)malloc(sz);
+    real* qx = (real*)malloc(sz);
+    real* qy = (real*)malloc(sz);
     for (int64_t i = 0; i < n; ++i) orc_prim_to_q(W + 4 * i, c->gamma, q + 4 * i);
     orc_q_derivatives(c, q, inner, qx, qy);
     int bad = orc_flux_residual(c, q, qx, qy, R);
