@@ -204,13 +204,6 @@ cudaError_t run_iteration(lskum_ctx* c, int64_t* launches) {
 
 cudaError_t refresh_mixed_q(lskum_ctx* c);
 
-// q-variables of the current U in both representations.
-cudaError_t launch_q_refresh(lskum_ctx* c) {
-    cudaError_t e = launch_q_from_U(c->g, c->ph, c->st.U, c->st.q[0], c->stream);
-    if (e != cudaSuccess) return e;
-    return refresh_mixed_q(c);
-}
-
 // After U changed from the host side: the mixed path's float-pair q.
 cudaError_t refresh_mixed_q(lskum_ctx* c) {
     if (!c->mixed) return cudaSuccess;
@@ -648,11 +641,14 @@ int lskum_info(lskum_ctx* c, int64_t* n_points, int64_t* n_wall, int* max_neighb
 int lskum_autotune(lskum_ctx* c, int trial_iters, int* best_block) {
     if (!c || trial_iters < 1) return fail(LSKUM_ERR_INVALID_ARG, "invalid argument");
     if (!c->have_state) return fail(LSKUM_ERR_STATE, "no state set");
-    // keep the state: every trial restarts from it
+    // keep the state (U and its FP64 q-variables, which set_state may have
+    // formed from the primitive state directly): every trial restarts from it
     V4* saved = nullptr;
     const size_t N = size_t(c->g.n) * c->C;
-    LSKUM_CUDA(cudaMalloc(&saved, sizeof(V4) * N));
+    LSKUM_CUDA(cudaMalloc(&saved, 2 * sizeof(V4) * N));
     LSKUM_CUDA(cudaMemcpyAsync(saved, c->st.U, sizeof(V4) * N, cudaMemcpyDeviceToDevice, c->stream));
+    LSKUM_CUDA(cudaMemcpyAsync(saved + N, c->st.q[0], sizeof(V4) * N, cudaMemcpyDeviceToDevice,
+                               c->stream));
     const int candidates[2] = {128, 256};
     double best_ms = 1e300;
     int best = c->block, best_ls = c->block_ls;
@@ -684,6 +680,8 @@ int lskum_autotune(lskum_ctx* c, int trial_iters, int* best_block) {
             }
             LSKUM_CUDA(cudaMemcpyAsync(c->st.U, saved, sizeof(V4) * N, cudaMemcpyDeviceToDevice,
                                        c->stream));
+            LSKUM_CUDA(cudaMemcpyAsync(c->st.q[0], saved + N, sizeof(V4) * N,
+                                       cudaMemcpyDeviceToDevice, c->stream));
         }
     }
     c->profiling = was_profiling;
@@ -693,9 +691,10 @@ int lskum_autotune(lskum_ctx* c, int trial_iters, int* best_block) {
     cudaFree(saved);
     c->block = best;
     c->block_ls = best_ls;
-    // the state is back to where it was: rebuild q, drop the captured graph
-    // (its launch shapes belong to the old block size) and the trial history
-    LSKUM_CUDA(launch_q_refresh(c));
+    // the state is back to where it was: rebuild the mixed path's q (from U,
+    // as set_state does), drop the captured graph (its launch shapes belong to
+    // the old block size) and the trial history
+    LSKUM_CUDA(refresh_mixed_q(c));
     if (c->graph_exec) {
         cudaGraphExecDestroy(c->graph_exec);
         c->graph_exec = nullptr;

@@ -174,17 +174,23 @@ __device__ __forceinline__ bool modified_states(const bool second, const double 
     return diff != 0;
 }
 
+// Eq. 26 from the primitive state (rho, u, v, p).
+__device__ __forceinline__ void prim_to_q(const double rho, const double u, const double v,
+                                          const double p, const Physics& ph, V4& q) {
+    const double beta = rho / (2.0 * p);
+    q.a = log(rho) + log(beta) * ph.gm1_inv - beta * (u * u + v * v);
+    q.b = 2.0 * beta * u;
+    q.c = 2.0 * beta * v;
+    q.d = -2.0 * beta;
+}
+
 __device__ __forceinline__ void cons_to_q(const V4& U, const Physics& ph, V4& q, double& rho,
                                           double& u, double& v, double& p) {
     rho = U.a;
     u = U.b / rho;
     v = U.c / rho;
     p = ph.gm1 * (U.d - 0.5 * rho * (u * u + v * v));
-    const double beta = rho / (2.0 * p);
-    q.a = log(rho) + log(beta) * ph.gm1_inv - beta * (u * u + v * v);
-    q.b = 2.0 * beta * u;
-    q.c = 2.0 * beta * v;
-    q.d = -2.0 * beta;
+    prim_to_q(rho, u, v, p, ph, q);
 }
 
 __device__ __forceinline__ bool physical(double rho, double u, double v, double p) {
@@ -589,9 +595,9 @@ __global__ void k_set_uniform(const DevGeom g, const Physics ph, const V4* __res
     u.c = W.a * W.c;
     u.d = W.d * ph.gm1_inv + 0.5 * W.a * (W.b * W.b + W.c * W.c);
     U[t] = u;
+    // q straight from the given primitive state (no round trip through U)
     V4 qq;
-    double rho, uu, vv, p;
-    cons_to_q(u, ph, qq, rho, uu, vv, p);
+    prim_to_q(W.a, W.b, W.c, W.d, ph, qq);
     q[t] = qq;
 }
 
@@ -610,9 +616,9 @@ __global__ void k_set_prim(const DevGeom g, const Physics ph, const V4* __restri
     u.c = W.a * W.c;
     u.d = W.d * ph.gm1_inv + 0.5 * W.a * (W.b * W.b + W.c * W.c);
     U[t] = u;
+    // q straight from the given primitive state (no round trip through U)
     V4 qq;
-    double rho, uu, vv, p;
-    cons_to_q(u, ph, qq, rho, uu, vv, p);
+    prim_to_q(W.a, W.b, W.c, W.d, ph, qq);
     q[t] = qq;
 }
 

@@ -7,7 +7,7 @@ import pytest
 
 from oracle import oracle as O
 from paper_2108_07031_gb300 import cloud as Cl
-from parity_utils import normwise, residual_conditioning_bound
+from parity_utils import describe, exact_errors, normwise
 
 pytestmark = pytest.mark.gpu
 
@@ -21,6 +21,14 @@ from paper_2108_07031_gb300 import lskum as L  # noqa: E402
 @pytest.fixture(scope="module")
 def cloud():
     return Cl.naca0012_cloud(130, 41, shuffle=True, seed=99)
+
+
+def _check_residual(oc, W, R, inner=2):
+    """One condition's FP64 residual: per component, at most twice the FP64
+    oracle's own 2-norm distance from the binary128 reference."""
+    errs = exact_errors(oc, W, {"R": R}, inner=inner)
+    print(describe(errs))
+    assert np.all(errs["R"]["gpu_rms"] <= 2.0 * errs["R"]["oracle_rms"])
 
 
 @pytest.mark.parametrize("precision", [L.FP64, L.MIXED])
@@ -73,8 +81,7 @@ def test_set_state_and_residual_layout(cloud):
         R = b.eval_residual()
     oc = O.OracleCloud.from_cloud(cloud)
     for k in range(2):
-        R_o, tol, spread = residual_conditioning_bound(oc, W[k])
-        assert normwise(R[k], R_o) < tol, (normwise(R[k], R_o), spread)
+        _check_residual(oc, W[k], R[k])
 
 
 @pytest.mark.parametrize("opts", [dict(weight_power=1.5, inner_iters=3),
@@ -96,8 +103,7 @@ def test_batched_option_variants_against_oracle(cloud, opts):
         b.step(3)
         W3 = b.get_state()
     for k in (0, 3):
-        R_o, tol, spread = residual_conditioning_bound(oc, W[k], inner=inner)
-        assert normwise(R[k], R_o) < tol, (k, normwise(R[k], R_o), spread)
+        _check_residual(oc, W[k], R[k], inner=inner)
         W3_o, _, st = O.iterate(oc, W[k], 3, inner=inner)
         assert st == 0
         assert normwise(W3[k], W3_o) < 1e-11
