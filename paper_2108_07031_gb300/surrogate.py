@@ -315,6 +315,10 @@ def predict_state(mlp: MLP, cloud, wall_d, mach, alpha_deg, arc=None):
     W = state_from_output(out, mach, alpha_deg)
     if not np.all(np.isfinite(W)) or np.any(W[:, 0] <= 0.05) or np.any(W[:, 3] <= 0.05):
         return None
+    # far-field points are boundary data, held at whatever state they are
+    # given: they keep the exact free stream (a predicted far field would fix
+    # a different circulation around the aerofoil for good)
+    W[cloud.flags == Cl.FLAG_OUTER] = freestream(mach, alpha_deg)
     # the wall condition holds no normal momentum: project the prediction
     wall = cloud.flags == Cl.FLAG_WALL
     n = cloud.normals[wall]

@@ -3,15 +3,17 @@ batched solver and measure what it gains over the free-stream start.
 
   python -m paper_2108_07031_gb300.warmstart_study [--out results.json]
 
-Cloud: the 5,120-point NACA 0012 cloud (128 x 40). Training: 256 seeded
-conditions, M ~ U[0.3, 0.8], alpha ~ U[-4, 6] deg, each solved by the
-batched mixed-precision solver (64 conditions per launch, CFL 0.8: the
-converged state does not depend on the pseudo-time step) to a 7-order
-residue drop. Network: the 6-layer, width-256 BF16 tensor-core MLP, Adam with
+Cloud: the NACA 0012 cloud of --cloud points (default 128 x 40 = 5,120).
+Training: --train seeded conditions (default 256), M ~ U[0.3, 0.8],
+alpha ~ U[-4, 6] deg, each solved by the batched mixed-precision solver (64
+conditions per launch, CFL 0.8: the converged state does not depend on the
+pseudo-time step) to a 7-order residue drop. Network: the 6-layer, width-256 BF16 tensor-core MLP, Adam with
 a cosine schedule. Evaluation: 32 held-out conditions (another seed), each
-solved from the free stream and from the network's prediction at the
-configuration's CFL 0.2; reported: iterations until the residue is 1e-6 of
-the free-stream start's first residue, and the converged Cl/Cd of both.
+solved from the free stream and from the network's prediction (whose
+far-field points keep the exact free stream: they are boundary data) at the
+configuration's CFL 0.2 (--eval-cfl); reported: iterations until the residue
+is 1e-6 of the free-stream start's first residue, and the converged Cl/Cd of
+both.
 """
 
 from __future__ import annotations
@@ -33,6 +35,9 @@ def main():
 
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default="warmstart_study.json")
+    ap.add_argument("--cloud", default="128x40", help="n_c x n_r of the NACA 0012 cloud")
+    ap.add_argument("--data-iters", type=int, default=40_000,
+                    help="iteration budget per batch of training solves")
     ap.add_argument("--train", type=int, default=256)
     ap.add_argument("--test", type=int, default=32)
     ap.add_argument("--epochs", type=int, default=240)
@@ -51,7 +56,8 @@ def main():
     prec = L.MIXED if args.precision == "mixed" else L.FP64
     log = lambda m: print(m, flush=True)  # noqa: E731
 
-    cloud = Cl.naca0012_cloud(128, 40)
+    n_c, n_r = (int(v) for v in args.cloud.lower().split("x"))
+    cloud = Cl.naca0012_cloud(n_c, n_r)
     wd = S.wall_distance(cloud)
     m_tr, a_tr = Cl.conditions(args.train, seed=2021)
     m_te, a_te = Cl.conditions(args.test, seed=4242)
@@ -59,7 +65,8 @@ def main():
     if args.data_cache and os.path.exists(args.data_cache):
         W_tr, it_tr = np.load(args.data_cache), []
     else:
-        W_tr, it_tr = S.converged_solutions(cloud, m_tr, a_tr, tol=1e-7, max_iters=40_000)
+        W_tr, it_tr = S.converged_solutions(cloud, m_tr, a_tr, tol=1e-7,
+                                            max_iters=args.data_iters)
         if args.data_cache:
             np.save(args.data_cache, W_tr)
     t_data = time.time() - t0
@@ -141,6 +148,11 @@ def main():
         "cd_cold": results["cold"]["cd"].tolist(), "cd_warm": results["warm"]["cd"].tolist(),
         "dcl_abs_mean": float(np.mean(np.abs(results["warm"]["cl"] - results["cold"]["cl"]))),
         "dcd_abs_mean": float(np.mean(np.abs(results["warm"]["cd"] - results["cold"]["cd"]))),
+        "dcl_abs_max": float(np.max(np.abs(results["warm"]["cl"] - results["cold"]["cl"]))),
+        "dcd_abs_max": float(np.max(np.abs(results["warm"]["cd"] - results["cold"]["cd"]))),
+        "residue_end_cold": results["cold"]["hist"][-1].tolist(),
+        "residue_end_warm": results["warm"]["hist"][-1].tolist(),
+        "eval_iters": args.eval_iters,
         "prediction_rel_err_max_mean": float(np.mean(pred_err)),
         "mach": m_te.tolist(), "alpha": a_te.tolist(),
     }
