@@ -221,7 +221,11 @@ int64_t lskum_last_launch_count(lskum_ctx* ctx);
  * inside the library (8192 partials of 8192 points each); every GPU that
  * loads the library holds that array until the process exits. The first call
  * on each device looks the array's device address up (no allocation); make
- * that first call before any stream capture. All calls on a device share the
+ * that first call before any stream capture. The address is kept for the life
+ * of the process: after cudaDeviceReset (or any other destruction of the
+ * device's primary context) the library's module is loaded again at another
+ * address and the kept one is stale, so do not call this entry point on a
+ * device after resetting it. All calls on a device share the
  * array and each call overwrites the part it reads, so nothing carries over
  * between calls, but calls that overlap on the GPU (different streams, no
  * ordering between them) race on it. Asynchronous: *out is ready when the

@@ -71,7 +71,10 @@ k_noalloc_final(const double* __restrict__ scratch, int nblocks, int64_t n, doub
 }
 
 // Device address of the scratch array on the current device, looked up once
-// per device (cudaGetSymbolAddress allocates nothing).
+// per device (cudaGetSymbolAddress allocates nothing) and kept for the life of
+// the process. A device reset reloads the module at another address, which
+// makes the kept address stale; the header states that the entry point is not
+// to be called on a device after it was reset.
 int scratch_for_current_device(double** ptr, std::string& err) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
