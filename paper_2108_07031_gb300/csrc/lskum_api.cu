@@ -348,18 +348,23 @@ int lskum_create(int64_t n, const double* xy, const double* normals, const int8_
             (e = upload(c, &g.lsum, lsum)) != cudaSuccess)
             return bail(e, "upload of the FP64 inner-sweep coefficients");
     } else {
-        // FP32 records per neighbour entry: {wx, wy, hdx, hdy} and {ws, wn, hdx, hdy}
-        std::vector<float4> lsw(L.wx.size()), fxw(L.wx.size());
+        // FP32 records per neighbour entry: {ws, wn, hdx, hdy} and {wx, wy};
+        // per point the coordinates as float pairs (device order)
+        std::vector<float4> fxw(L.wx.size());
         std::vector<float2> lw2(L.wx.size());
-        for (size_t i = 0; i < lsw.size(); ++i) {
-            const float hx = float(L.hdx[i]), hy = float(L.hdy[i]);
-            lsw[i] = make_float4(float(L.wx[i]), float(L.wy[i]), hx, hy);
-            fxw[i] = make_float4(float(L.ws[i]), float(L.wn[i]), hx, hy);
-            lw2[i] = make_float2(lsw[i].x, lsw[i].y);
+        for (size_t i = 0; i < fxw.size(); ++i) {
+            fxw[i] = make_float4(float(L.ws[i]), float(L.wn[i]), float(L.hdx[i]), float(L.hdy[i]));
+            lw2[i] = make_float2(float(L.wx[i]), float(L.wy[i]));
         }
-        if ((e = upload(c, &c->g32.lsw, lsw)) != cudaSuccess ||
-            (e = upload(c, &c->g32.fxw, fxw)) != cudaSuccess ||
-            (e = upload(c, &c->g32.lw2, lw2)) != cudaSuccess)
+        std::vector<float4> xyhl(size_t(L.n));
+        for (int64_t d = 0; d < L.n; ++d) {
+            const double x = xy[2 * size_t(L.dev_to_user[d])], y = xy[2 * size_t(L.dev_to_user[d]) + 1];
+            const float xh = float(x), yh = float(y);
+            xyhl[size_t(d)] = make_float4(xh, yh, float(x - double(xh)), float(y - double(yh)));
+        }
+        if ((e = upload(c, &c->g32.fxw, fxw)) != cudaSuccess ||
+            (e = upload(c, &c->g32.lw2, lw2)) != cudaSuccess ||
+            (e = upload(c, &c->g32.xyhl, xyhl)) != cudaSuccess)
             return bail(e, "upload of the FP32 cloud layout");
     }
 

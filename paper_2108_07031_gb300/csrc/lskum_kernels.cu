@@ -42,8 +42,8 @@ constexpr int64_t kSignBit = int64_t(0x8000000000000000ULL);
 constexpr int64_t kAbsMask = 0x7FFFFFFFFFFFFFFFLL;
 constexpr int64_t kBits700 = 0x4085E00000000000LL;  // 700.0
 constexpr int64_t kBits6 = 0x4018000000000000LL;    // 6.0, the end of the erfcx table
-static_assert(kErfcxLo == 0.0 && kErfcxInvW == 8.0 && kErfcxHi == 6.0,
-              "erfcx_piece assumes 1/8-wide pieces on [0, 6]");
+static_assert(kErfcxLo == 0.0 && kErfcxInvW == double(1 << kErfcxLog2InvW) && kErfcxHi == 6.0,
+              "erfcx_piece assumes pieces of width 2^-kErfcxLog2InvW on [0, 6]");
 
 __device__ __forceinline__ int64_t dbits(const double x) { return __double_as_longlong(x); }
 __device__ __forceinline__ double bitsd(const int64_t b) { return __longlong_as_double(b); }
@@ -55,25 +55,26 @@ struct Prim {
     double r, u, v, p, sb, cb, h, k;
 };
 
-// exp(x) 2^-HALVE by Tang's table-driven method (math_tables.h): x = k ln2/64
-// + r, |r| <= ln2/128, exp(x) = 2^(k>>6) 2^((k&63)/64) e^r with e^r - 1 from
-// its degree-5 Taylor polynomial (remainder < 4e-17); max error 1.2 ulp
-// (checked against 400-bit arithmetic with exact FMA emulation). About 10
-// FP64 operations against the library's ~18; the power of two, including
-// the optional halving, is an integer add to the exponent field (the result
-// stays normal for |x| <= 700). Outside that range the library exp.
+// exp(x) 2^-HALVE by Tang's table-driven method (math_tables.h): x = k ln2/N
+// + r (N = 2^kExpBits = 256), |r| <= ln2/(2N), exp(x) = 2^(k div N)
+// 2^((k mod N)/N) e^r with e^r - 1 from its degree-4 Taylor polynomial
+// (remainder < 4e-17); max error 1.2 ulp (checked against 200-bit arithmetic
+// with exact FMA emulation). About 9 FP64 operations against the library's
+// ~18; the power of two, including the optional halving, is an integer add
+// to the exponent field (the result stays normal for |x| <= 700). Outside
+// that range the library exp.
 template <int HALVE>
 __device__ __forceinline__ double exp_tab(const double x) {
     if ((dbits(x) & kAbsMask) > kBits700) return HALVE ? 0.5 * exp(x) : exp(x);
     const double shifter = 6755399441055744.0;  // 1.5 * 2^52: rounds k into the low bits
-    double kd = fma(x, kInvLn2By64, shifter);
+    double kd = fma(x, kInvLn2ByN, shifter);
     const int64_t k = dbits(kd) - 0x4338000000000000LL;
     kd -= shifter;
-    const double r = fma(-kd, kLn2By64Lo, fma(-kd, kLn2By64Hi, x));
-    const double p = r * fma(r, fma(r, fma(r, fma(r, 1.0 / 120.0, 1.0 / 24.0), 1.0 / 6.0), 0.5), 1.0);
-    const double t = kExp2Tab[k & 63];
+    const double r = fma(-kd, kLn2ByNLo, fma(-kd, kLn2ByNHi, x));
+    const double p = r * fma(r, fma(r, fma(r, 1.0 / 24.0, 1.0 / 6.0), 0.5), 1.0);
+    const double t = kExp2Tab[k & ((1 << kExpBits) - 1)];
     const double res = fma(t, p, t);
-    return bitsd(dbits(res) + (((k >> 6) - HALVE) << 52));
+    return bitsd(dbits(res) + (((k >> kExpBits) - HALVE) << 52));
 }
 
 // q~ -> primitive (inverse of Eq. 26); velocities in the global frame. With
@@ -88,13 +89,13 @@ __device__ __forceinline__ Prim q_to_prim(const double t0, const double t1, cons
     const double isb = rsqrt(beta);
     w.sb = beta * isb;
     w.cb = isb * kInvSqrtPi;
-    // 1/(2 beta) = -1/q4 by an IEEE (correctly rounded) division: u, v, p and
-    // the density's (1/beta)^2 inherit its accuracy. Forming it from
-    // (1/sqrt(beta))^2 is 3 % faster but adds ~2 ulp to every primitive,
-    // which the split-flux differences of Eq. 24 amplify to ~1e-12 relative
-    // in the residual on 5k-point clouds.
-    const double inv2b = -1.0 / t3;
-    const double i2 = 2.0 * inv2b;   // 1 / beta
+    // 1/beta from (1/sqrt(beta))^2 and one Newton step, i2 (1 + (1 - beta
+    // i2)): the residual 1 - beta i2 comes exact from the FMA, so the step
+    // leaves ~0.5 ulp, as good as an IEEE division (u, v, p and the density's
+    // (1/beta)^2 inherit it) for 4 FP64 instructions instead of ~7.
+    const double i20 = isb * isb;
+    const double i2 = fma(i20, fma(-beta, i20, 1.0), i20);  // 1 / beta
+    const double inv2b = 0.5 * i2;                         // 1 / (2 beta)
     w.u = t1 * inv2b;
     w.v = t2 * inv2b;
     const double uu = fma(w.u, w.u, w.v * w.v);
@@ -110,10 +111,11 @@ __device__ __forceinline__ Prim q_to_prim(const double t0, const double t1, cons
     return w;
 }
 
-// Index of the 1/8-wide erfcx piece holding a (0 <= a <= 6), floor(8 a),
-// from the bit pattern of a = 1.f x 2^e: 8 a = (2^52 + f) / 2^(49 - e).
+// Index of the erfcx piece holding a (0 <= a <= 6), floor(2^L a) with
+// L = kErfcxLog2InvW, from the bit pattern of a = 1.f x 2^e:
+// 2^L a = (2^52 + f) / 2^(52 - L - e).
 __device__ __forceinline__ int erfcx_piece(const int64_t abits) {
-    const int sh = 49 - (int(abits >> 52) - 1023);
+    const int sh = (52 - kErfcxLog2InvW) - (int(abits >> 52) - 1023);
     const int64_t m = (abits & 0x000FFFFFFFFFFFFFLL) | 0x0010000000000000LL;
     const int k = sh > 52 ? 0 : int(m >> sh);
     return min(k, kErfcxPieces - 1);

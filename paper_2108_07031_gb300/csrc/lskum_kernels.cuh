@@ -33,11 +33,16 @@ struct __align__(32) D8f {
 
 // FP32 copies of the slot-major per-neighbour arrays (mixed precision).
 struct DevGeom32 {
-    // slot-major [slot][stride], one 16-byte record per neighbour entry so a
-    // kernel fetches its per-neighbour constants with one vector load
-    const float4* lsw;  // {wx, wy, hdx, hdy}: least-squares weights (Eq. 11), half offsets
+    // slot-major [slot][stride], one record per neighbour entry so a kernel
+    // fetches its per-neighbour constants with one vector load
     const float4* fxw;  // {ws, wn, hdx, hdy}: split-stencil weights (Eq. 24), half offsets
-    const float2* lw2;  // {wx, wy} alone, for the first-order sweep
+    const float2* lw2;  // {wx, wy}: least-squares weights (Eq. 11), both q-derivative sweeps
+    // per point (device order): the coordinates as float pairs {x hi, y hi,
+    // x lo, y lo} (hi + lo = the FP64 coordinate to ~2^-48), so the inner
+    // sweeps form the half offsets (P_j - P_i)/2 in FP32 to FP32 precision of
+    // the offset itself, from a gathered 16-byte record, instead of streaming
+    // them per neighbour entry
+    const float4* xyhl;
 };
 
 // Static cloud data on the device (device point order).

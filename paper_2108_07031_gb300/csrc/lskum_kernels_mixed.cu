@@ -70,7 +70,10 @@ __global__ void __launch_bounds__(BLOCK) k_ls_first_mx(const DevGeom g, const De
 // (dq_first, the sum of wx_j (q_j - q_i)) minus the sum of wx_j (hdx_j
 // (qx_j - qx_i) + hdy_j (qy_j - qy_i)): the q gathers and their float-pair
 // differences are done once per stage, not per sweep; the derivative
-// differences stay differences (exact in FP32 for nearby values).
+// differences stay differences (exact in FP32 for nearby values). The
+// per-neighbour stream is the 8-byte weight pair; the half offsets come from
+// the gathered coordinate pairs of the neighbour (cache-resident: the
+// neighbours of a warp's points are close in the Hilbert order).
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK) k_ls_inner_mx(const DevGeom g, const DevGeom32 g32,
                                                        const D8f* __restrict__ dq_first,
@@ -81,13 +84,18 @@ __global__ void __launch_bounds__(BLOCK) k_ls_inner_mx(const DevGeom g, const De
     const uint32_t cc = uint32_t(t) & g.cmask;
     if (d >= g.n) return;
     const D8f di = din[t];
+    const float4 pi = g32.xyhl[d];
     float4 ax = make_float4(0.f, 0.f, 0.f, 0.f), ay = ax;
     const int c = g.cnt[d];
+#pragma unroll 4
     for (int k = 0; k < c; ++k) {
         const int64_t at = int64_t(k) * g.stride + d;
         const uint32_t j = g.nbr[at] & kIndexMask;
-        const float4 lw = g32.lsw[at];
-        const float wx = lw.x, wy = lw.y, hx = lw.z, hy = lw.w;
+        const float2 lw = g32.lw2[at];
+        const float4 pj = g32.xyhl[j];
+        const float wx = lw.x, wy = lw.y;
+        const float hx = 0.5f * ((pj.x - pi.x) + (pj.z - pi.z));
+        const float hy = 0.5f * ((pj.y - pi.y) + (pj.w - pi.w));
         const D8f dj = din[sidx(g, j, cc)];
         // (dx (qx_j - qx_i) + dy (qy_j - qy_i)) / 2, the Eq. 28 correction
         const float t0 = hx * (dj.x.x - di.x.x) + hy * (dj.y.x - di.y.x);
@@ -108,7 +116,30 @@ struct PrimPair {
     float r, u, v, p, sb;       // base state (of q~_0): density, velocity, pressure, sqrt(beta)
     float dr, du, dv, dp, dsb;  // difference state(q~_j) - state(q~_0)
     float isb, isbj;            // 1/sqrt(beta) of the base and of state j
+    // frame-invariant factors both split fluxes of the pair share (base and
+    // difference): p + rho e and rho e + p/2
+    float h, dh, k, dk;
 };
+
+// e^x - 1: its Taylor polynomial to x^5/120 for |x| <= 1/16 (the remainder is
+// below 2e-9 of the result), the library function beyond. The arguments
+// here are differences of nearby states, almost always far inside 1/16.
+__device__ __forceinline__ float expm1_f(const float x) {
+    if (fabsf(x) <= 0.0625f)
+        return x * fmaf(x, fmaf(x, fmaf(x, fmaf(x, 1.0f / 120.0f, 1.0f / 24.0f), 1.0f / 6.0f), 0.5f),
+                        1.0f);
+    return expm1f(x);
+}
+
+// ln(1 + x): its Taylor polynomial to x^6/6 for |x| <= 1/16 (remainder below
+// 1e-8 of the result), the library function beyond.
+__device__ __forceinline__ float log1p_f(const float x) {
+    if (fabsf(x) <= 0.0625f)
+        return x * fmaf(x, fmaf(x, fmaf(x, fmaf(x, fmaf(x, -1.0f / 6.0f, 0.2f), -0.25f), 1.0f / 3.0f),
+                                -0.5f),
+                        1.0f);
+    return log1pf(x);
+}
 
 // The FP32 quotients below are fast (reciprocal approximation times the
 // numerator, ~2 ulp): every one scales a difference term, whose own FP32
@@ -145,27 +176,38 @@ __device__ __forceinline__ PrimPair prim_pair(const float4 b, const float4 dq, c
     } else {
         w.r = __expf(b.x - __logf(beta) * gm1_inv + beta * uu0);
     }
-    const float dlnr = dq.x - log1pf(dbeta * (2.0f * inv2b)) * gm1_inv + (dbeta * uuj + beta * duu);
-    w.dr = w.r * expm1f(dlnr);
+    const float dlnr = dq.x - log1p_f(dbeta * (2.0f * inv2b)) * gm1_inv + (dbeta * uuj + beta * duu);
+    w.dr = w.r * expm1_f(dlnr);
     // p = rho / (2 beta):  p_j - p_0 = (drho beta - rho dbeta) / (2 beta beta_j)
     w.p = w.r * inv2b;
     w.dp = (w.dr * beta - w.r * dbeta) * (inv2b * (w.isbj * w.isbj));
+    // rho e = p/(gamma-1) + rho |u|^2 / 2 (|u|^2 is the same in every frame)
+    const float E0 = w.p * gm1_inv + 0.5f * w.r * uu0;
+    const float dE = w.dp * gm1_inv + 0.5f * (w.dr * uuj + w.r * duu);
+    w.h = w.p + E0;
+    w.dh = w.dp + dE;
+    w.k = E0 + 0.5f * w.p;
+    w.dk = dE + 0.5f * w.dp;
     return w;
 }
 
 // erfc(m - h) - erfc(m + h) = (4/sqrt(pi)) e^{-m^2} (h + H2 h^3/6 + H4 h^5/120
 // + H6 h^7/5040 + H8 h^9/362880) with the Hermite polynomials H_k(m): the
 // even Taylor terms of e^{-t^2} about m integrated over [m - h, m + h].
+// For |h| <= 1/64 the H6 and H8 terms are below 2e-11 of the first (|m| <=
+// 6.5, the range where erfc is not negligible) and are left out.
 __device__ __forceinline__ float erfc_central_diff(const float m, const float h) {
     const float m2 = m * m;
     const float H2 = 4.0f * m2 - 2.0f;
     const float H4 = (16.0f * m2 - 48.0f) * m2 + 12.0f;
-    const float H6 = ((64.0f * m2 - 480.0f) * m2 + 720.0f) * m2 - 120.0f;
-    const float H8 = (((256.0f * m2 - 3584.0f) * m2 + 13440.0f) * m2 - 13440.0f) * m2 + 1680.0f;
     const float h2 = h * h;
-    const float s = h * (1.0f + h2 * (H2 * (1.0f / 6.0f) +
-                                      h2 * (H4 * (1.0f / 120.0f) +
-                                            h2 * (H6 * (1.0f / 5040.0f) + h2 * (H8 * (1.0f / 362880.0f))))));
+    float tail = H4 * (1.0f / 120.0f);
+    if (fabsf(h) > 0.015625f) {
+        const float H6 = ((64.0f * m2 - 480.0f) * m2 + 720.0f) * m2 - 120.0f;
+        const float H8 = (((256.0f * m2 - 3584.0f) * m2 + 13440.0f) * m2 - 13440.0f) * m2 + 1680.0f;
+        tail += h2 * (H6 * (1.0f / 5040.0f) + h2 * (H8 * (1.0f / 362880.0f)));
+    }
+    const float s = h * (1.0f + h2 * (H2 * (1.0f / 6.0f) + h2 * tail));
     return 4.0f * kInvSqrtPiF * __expf(-m2) * s;
 }
 
@@ -188,20 +230,21 @@ __device__ __forceinline__ float half_erfc_f(const float x, const float e) {
     return x > 0.0f ? hc : 1.0f - hc;
 }
 
-// Difference of the kinetic split flux along the frame's first axis, sign sg:
-// dG = G(state_j) - G(state_0), state_j = base + difference.
-__device__ __forceinline__ void dsplit_flux_a(const float r0, const float ua0, const float ub0,
-                                              const float p0, const float sb0, const float dr,
-                                              const float dua, const float dub, const float dp,
-                                              const float dsb, const float isb0, const float isbj,
-                                              const float sg, const float gm1_inv, float dG[4]) {
+// Difference of the kinetic split flux along the frame's first axis ("a",
+// velocity ua, transverse ub), sign sg: dG = G(state_j) - G(state_0),
+// state_j = base + difference; the frame-invariant factors come from w.
+__device__ __forceinline__ void dsplit_flux_a(const PrimPair& w, const float ua0, const float ub0,
+                                              const float dua, const float dub, const float sg,
+                                              float dG[4]) {
+    const float r0 = w.r, dr = w.dr, p0 = w.p, dp = w.dp, sb0 = w.sb, dsb = w.dsb;
+    const float isb0 = w.isb, isbj = w.isbj;
     const float uaj = ua0 + dua, ubj = ub0 + dub, sbj = sb0 + dsb;
     const float S0 = ua0 * sb0;
     const float dS = dua * sbj + ua0 * dsb;
     const float Sj = S0 + dS;
     // exponential: e_j - e_0 = e_0 expm1(-(S_j^2 - S_0^2))
     const float e0 = __expf(-S0 * S0);
-    const float de = e0 * expm1f(-dS * (Sj + S0));
+    const float de = e0 * expm1_f(-dS * (Sj + S0));
     // A = erfc(x)/2 at x = -sg S
     const float x0 = -sg * S0, dx = -sg * dS;
     const float A0 = half_erfc_f(x0, e0);  // e0 = exp(-x0^2)
@@ -218,12 +261,6 @@ __device__ __forceinline__ void dsplit_flux_a(const float r0, const float ua0, c
     const float B0 = c * e0 * isb0;
     const float dB = c * (de * isbj - e0 * dsb * isbj * isb0);
     const float Bj = B0 + dB;
-    // rho e = p/(gamma-1) + rho |u|^2 / 2
-    const float uu0 = ua0 * ua0 + ub0 * ub0;
-    const float uuj = uaj * uaj + ubj * ubj;
-    const float duu = dua * (uaj + ua0) + dub * (ubj + ub0);
-    const float E0 = p0 * gm1_inv + 0.5f * r0 * uu0;
-    const float dE = dp * gm1_inv + 0.5f * (dr * uuj + r0 * duu);
     // t = u_a A + sg B
     const float t0 = ua0 * A0 + sg * B0;
     const float dt = dua * Aj + ua0 * dA + sg * dB;
@@ -241,11 +278,34 @@ __device__ __forceinline__ void dsplit_flux_a(const float r0, const float ua0, c
     const float drb = dr * ubj + r0 * dub;
     dG[2] = drb * tj + rb0 * dt;
     // energy: (p + rho e) u_a A + sg (rho e + p/2) B
-    const float Q0 = (p0 + E0) * ua0;
-    const float dQ = (dp + dE) * uaj + (p0 + E0) * dua;
-    const float Rr0 = E0 + 0.5f * p0;
-    const float dRr = dE + 0.5f * dp;
-    dG[3] = dQ * Aj + Q0 * dA + sg * (dRr * Bj + Rr0 * dB);
+    const float Q0 = w.h * ua0;
+    const float dQ = w.dh * uaj + w.h * dua;
+    dG[3] = dQ * Aj + Q0 * dA + sg * (w.dk * Bj + w.k * dB);
+}
+
+// Natural logarithm by the table of math_tables.h (Tang-style reduction):
+// x = 2^e m, m in [1, 2), c_j the midpoint of m's 1/128 interval, F_j = 1/c_j
+// rounded, r = m F_j - 1 from one fused multiply-add (|r| <= 2^-8), log x =
+// e ln2 - log F_j + log1p(r) with the degree-6 Taylor polynomial of log1p
+// (remainder below 2e-18) and ln2, -log F_j as pairs of doubles. About 12
+// FP64 operations against the library's ~33 (this epilogue runs on the FP64
+// pipe, the mixed flux kernel's bound). Positive normal arguments only: the
+// rest (zero, subnormal, negative, non-finite: a diverged state) goes to the
+// library function.
+__device__ __forceinline__ double log_tab(const double x) {
+    const int64_t b = __double_as_longlong(x);
+    if (uint64_t(b - 0x0010000000000000LL) >= uint64_t(0x7FE0000000000000LL)) return log(x);
+    const double e = double(int(b >> 52) - 1023);
+    const double* t = kLogTab[int(b >> (52 - kLogBits)) & ((1 << kLogBits) - 1)];
+    const double m = __longlong_as_double((b & 0x000FFFFFFFFFFFFFLL) | 0x3FF0000000000000LL);
+    const double r = fma(m, __ldg(t), -1.0);
+    double p = fma(r, -1.0 / 6.0, 0.2);
+    p = fma(r, p, -0.25);
+    p = fma(r, p, 1.0 / 3.0);
+    p = fma(r, p, -0.5);
+    p = fma(r, p, 1.0);
+    p *= r;
+    return fma(e, kLn2Hi, __ldg(t + 1) + (p + fma(e, kLn2Lo, __ldg(t + 2))));
 }
 
 // q-variables (Eq. 26) from the conserved state, FP64 (the float-pair split
@@ -271,9 +331,9 @@ __device__ __forceinline__ void cons_to_q64(const V4& U, const Physics& ph, V4& 
     if (G14) {
         const double beta = 0.5 * rho * ip;
         const double b2 = beta * beta;
-        q.a = 0.5 * log((rho * rho) * (b2 * b2 * beta)) - bu2;
+        q.a = 0.5 * log_tab((rho * rho) * (b2 * b2 * beta)) - bu2;
     } else {
-        q.a = log(rho) + log(0.5 * rho * ip) * ph.gm1_inv - bu2;
+        q.a = log_tab(rho) + log_tab(0.5 * rho * ip) * ph.gm1_inv - bu2;
     }
     q.b = U.b * ip;
     q.c = U.c * ip;
@@ -376,16 +436,14 @@ __global__ void __launch_bounds__(BLOCK, 896 / BLOCK) k_flux_mx(const DevGeom g,
                 if (sc) {
                     const float sg = sc == 1u ? 1.f : -1.f;
                     float dG[4];
-                    dsplit_flux_a(w.r, w.u, w.v, w.p, w.sb, w.dr, w.du, w.dv, w.dp, w.dsb, w.isb, w.isbj, sg,
-                                  gm1_inv, dG);
+                    dsplit_flux_a(w, w.u, w.v, w.du, w.dv, sg, dG);
                     const float wt = fw.x;
                     R[0] += wt * dG[0]; R[1] += wt * dG[1]; R[2] += wt * dG[2]; R[3] += wt * dG[3];
                 }
                 if (nc) {
                     const float sg = nc == 1u ? 1.f : -1.f;
                     float dG[4];
-                    dsplit_flux_a(w.r, w.v, w.u, w.p, w.sb, w.dr, w.dv, w.du, w.dp, w.dsb, w.isb, w.isbj, sg,
-                                  gm1_inv, dG);
+                    dsplit_flux_a(w, w.v, w.u, w.dv, w.du, sg, dG);
                     const float wt = fw.y;
                     R[0] += wt * dG[0]; R[1] += wt * dG[2]; R[2] += wt * dG[1]; R[3] += wt * dG[3];
                 }
@@ -403,11 +461,16 @@ __global__ void __launch_bounds__(BLOCK, 896 / BLOCK) k_flux_mx(const DevGeom g,
         } else {
             V4 U = st.U[t];
             double dtv;
-            if (MODE == 1) {  // local time step (one division, two square roots)
-                const double irho = 1.0 / U.a;
-                const double u = U.b * irho, v = U.c * irho;
-                const double p = ph.gm1 * fma(-0.5 * U.a, fma(u, u, v * v), U.d);
-                dtv = ph.cfl * g.dmin[d] / (sqrt(fma(u, u, v * v)) + sqrt(ph.gamma * p * irho));
+            if (MODE == 1) {
+                // local time step in FP32: it sets the pseudo-time path, not
+                // the steady state, and FP32 square roots and quotients cost
+                // a fraction of the FP64 pipe's
+                const float rho = float(U.a), irho = 1.0f / rho;
+                const float u = float(U.b) * irho, v = float(U.c) * irho;
+                const float uu = fmaf(u, u, v * v);
+                const float p = float(ph.gm1) * (float(U.d) - 0.5f * rho * uu);
+                dtv = double(float(ph.cfl * g.dmin[d]) /
+                             (sqrtf(uu) + sqrtf(float(ph.gamma) * p * irho)));
                 st.dt[t] = dtv;
                 st.U0[t] = U;
                 r2 = R0 * R0;

@@ -216,6 +216,10 @@ class Solver:
         """set_state from a host address (e.g. a pinned torch tensor's data_ptr)."""
         _check(self._lib.lskum_set_state(self._h, C.c_void_p(host_ptr)), "lskum_set_state")
 
+    def get_state_ptr(self, host_ptr: int):
+        """get_state into a host address (e.g. a pinned torch tensor's data_ptr)."""
+        _check(self._lib.lskum_get_state(self._h, C.c_void_p(host_ptr)), "lskum_get_state")
+
     def get_state(self) -> np.ndarray:
         W = np.empty(self._shape(), dtype=np.float64)
         _check(self._lib.lskum_get_state(self._h, _ptr(W)), "lskum_get_state")

@@ -1,9 +1,11 @@
-"""Accuracy of the FP64 flux kernel's transcendental designs, checked on the
-CPU: the table-driven exponential (Tang's reduction with the 2^(j/64) table
-and a degree-5 polynomial) and erfc(a)/2 = exp(-a^2)/2 erfcx(a) from the
-erfcx pieces, both evaluated as the kernel does -- every fused multiply-add
-rounded once, emulated in 200-bit arithmetic -- against mpmath at 50
-digits, with the table values read from math_tables.h. CPU only."""
+"""Accuracy of the FP64 kernels' transcendental designs, checked on the CPU:
+the table-driven exponential (Tang's reduction with the 2^(j/256) table and
+a degree-4 polynomial), erfc(a)/2 = exp(-a^2)/2 erfcx(a) from the erfcx
+pieces, 1/beta from (1/sqrt(beta))^2 with one Newton step, and the
+table-driven logarithm of the mixed path's FP64 epilogue, all evaluated
+as the kernel does -- every fused multiply-add rounded once, emulated in
+200-bit arithmetic -- against mpmath at 50 digits, with the table values
+read from math_tables.h. CPU only."""
 
 import math
 import os
@@ -23,13 +25,20 @@ HDR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
 def tables():
     src = open(HDR).read()
     num = lambda name: float(re.search(name + r" = ([^;]+);", src).group(1))  # noqa: E731
-    exp_tab = [float(v) for v in re.search(r"kExp2Tab\[64\] = \{(.*?)\};", src, re.S).group(1)
+    exp_tab = [float(v) for v in re.search(r"kExp2Tab\[\d+\] = \{(.*?)\};", src, re.S).group(1)
                .replace("\n", "").split(",") if v.strip()]
     body = re.search(r"kErfcxC\[kErfcxPieces\]\[kErfcxDeg \+ 2\] = \{(.*?)\n\};", src, re.S).group(1)
     pieces = [[float(x) for x in row.split(",") if x.strip()]
               for row in re.findall(r"\{([^{}]*)\}", body)]
-    return {"hi": num("kLn2By64Hi"), "lo": num("kLn2By64Lo"), "inv": num("kInvLn2By64"),
-            "exp2": exp_tab, "pieces": pieces}
+    bits = int(num("kExpBits"))
+    assert len(exp_tab) == 1 << bits
+    log_body = re.search(r"kLogTab\[\d+\]\[4\] = \{(.*?)\n\};", src, re.S).group(1)
+    log_rows = [[float(x) for x in row.split(",") if x.strip()]
+                for row in re.findall(r"\{([^{}]*)\}", log_body)]
+    return {"hi": num("kLn2ByNHi"), "lo": num("kLn2ByNLo"), "inv": num("kInvLn2ByN"),
+            "exp2": exp_tab, "bits": bits, "pieces": pieces, "log2_inv_w": int(num("kErfcxLog2InvW")),
+            "log": log_rows, "log_bits": int(num("kLogBits")), "ln2_hi": num("kLn2Hi"),
+            "ln2_lo": num("kLn2Lo")}
 
 
 def _fma(a, b, c):
@@ -52,13 +61,13 @@ def _exp_tab(t, x, halve=0):
     k = _bits(kd) - 0x4338000000000000
     kd = kd - shifter
     r = _fma(-kd, t["lo"], _fma(-kd, t["hi"], x))
-    p = 1.0 / 120.0
-    for c in (1.0 / 24.0, 1.0 / 6.0, 0.5, 1.0):
+    p = 1.0 / 24.0
+    for c in (1.0 / 6.0, 0.5, 1.0):
         p = _fma(r, p, c)
     p = r * p
-    tj = t["exp2"][k & 63]
+    tj = t["exp2"][k & ((1 << t["bits"]) - 1)]
     res = _fma(tj, p, tj)
-    return _from_bits(_bits(res) + (((k >> 6) - halve) << 52))
+    return _from_bits(_bits(res) + (((k >> t["bits"]) - halve) << 52))
 
 
 def _ulp(x):
@@ -79,16 +88,17 @@ def test_table_exp_within_1_2_ulp(tables):
 
 
 def test_erfc_from_erfcx_pieces(tables):
-    """erfc(a)/2 for 0 <= a <= 6: piece floor(8a), Horner in (a - c_k), times
+    """erfc(a)/2 for 0 <= a <= 6: piece floor(2^L a), Horner in (a - c_k), times
     exp(-a^2)/2 from the table exponential. The argument -a^2 is rounded
     (like the exp(-S^2) of the B term in the oracle), so the relative error
     may grow as (1 + a^2) ulp: it stays within 4 (1 + a^2) ulp."""
     rng = np.random.Generator(np.random.PCG64(4))
     pieces = tables["pieces"]
     worst = 0.0
-    for a in np.concatenate([rng.uniform(0.0, 6.0, 1500), [0.0, 0.125, 0.5, 5.999999]]):
+    scale = float(1 << tables["log2_inv_w"])
+    for a in np.concatenate([rng.uniform(0.0, 6.0, 1500), [0.0, 0.125, 0.5, 1 / 64, 5.999999, 6.0]]):
         a = float(a)
-        c = pieces[min(int(math.floor(8.0 * a)), len(pieces) - 1)]
+        c = pieces[min(int(math.floor(scale * a)), len(pieces) - 1)]
         z = a - c[0]
         pv = c[-1]
         for coef in reversed(c[1:-1]):
@@ -99,3 +109,57 @@ def test_erfc_from_erfcx_pieces(tables):
         rel = float(abs(mp.mpf(got) - ref) / ref)
         worst = max(worst, rel / ((1.0 + a * a) * np.finfo(float).eps))
     assert worst < 4.0, worst
+
+
+def test_reciprocal_from_rsqrt_with_one_newton_step():
+    """1/beta = i (1 + (1 - beta i)) with i = (1/sqrt(beta))^2, the square root
+    reciprocal off by up to 2 ulp (the device's rsqrt is within 1): within
+    1 ulp of 1/beta, as an IEEE division is within 0.5."""
+    rng = np.random.Generator(np.random.PCG64(5))
+    worst = 0.0
+    for beta in np.concatenate([rng.uniform(0.05, 20.0, 2000), [0.5, 1.0, 0.7]]):
+        beta = float(beta)
+        for off in (-2, 0, 2):
+            isb = float(1 / mp.sqrt(mp.mpf(beta)))
+            for _ in range(abs(off)):
+                isb = math.nextafter(isb, math.inf if off > 0 else -math.inf)
+            i0 = isb * isb
+            i2 = _fma(i0, _fma(-beta, i0, 1.0), i0)
+            ref = 1 / mp.mpf(beta)
+            worst = max(worst, float(abs(mp.mpf(i2) - ref)) / _ulp(float(ref)))
+    assert worst <= 1.0, worst
+
+
+def _log_tab(t, x):
+    b = _bits(x)
+    e = float((b >> 52) - 1023)
+    row = t["log"][(b >> (52 - t["log_bits"])) & ((1 << t["log_bits"]) - 1)]
+    m = _from_bits((b & 0x000FFFFFFFFFFFFF) | 0x3FF0000000000000)
+    r = _fma(m, row[0], -1.0)
+    p = _fma(r, -1.0 / 6.0, 0.2)
+    for c in (-0.25, 1.0 / 3.0, -0.5, 1.0):
+        p = _fma(r, p, c)
+    p = p * r
+    return _fma(e, t["ln2_hi"], row[1] + (p + _fma(e, t["ln2_lo"], row[2])))
+
+
+def test_table_log(tables):
+    """log x within 0.5 ulp of max(|log x|, 1) -- an absolute bound at the
+    rounding of the O(1) q-variable it feeds; near x = 1 the reduction's
+    e ln2 and -log F_j cancel, so the bound is absolute -- and within 2 ulp
+    relative where |log x| > 0.1. Also the reduction constants the generator
+    states: ln2 split with a 42-bit high part."""
+    assert len(tables["log"]) == 1 << tables["log_bits"]
+    assert (mp.mpf(tables["ln2_hi"]) * 2 ** 42) % 1 == 0
+    rng = np.random.Generator(np.random.PCG64(6))
+    xs = np.concatenate([np.exp(rng.uniform(-30.0, 30.0, 2500)), 1.0 + rng.uniform(-1e-3, 1e-3, 500),
+                         [1.0, 0.5, 2.0, 0.168, 1.0 - 2 ** -53, 1.0 + 2 ** -52, 1e-300, 1e300]])
+    worst_abs = worst_rel = 0.0
+    for x in xs:
+        x = float(x)
+        ref = mp.log(mp.mpf(x))
+        err = float(abs(mp.mpf(_log_tab(tables, x)) - ref))
+        worst_abs = max(worst_abs, err / _ulp(max(abs(float(ref)), 1.0)))
+        if abs(float(ref)) > 0.1:
+            worst_rel = max(worst_rel, err / _ulp(abs(float(ref))))
+    assert worst_abs <= 0.5 and worst_rel <= 2.0, (worst_abs, worst_rel)
