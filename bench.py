@@ -41,6 +41,8 @@ METRIC = "q-LSKUM point-iterations/s (FP64 vs mixed vs batched), % of HBM roofli
 UNIT = "point-iterations/s"
 WORKLOAD_POINTS = 10_000_000
 MACH, ALPHA = 0.63, 2.0
+VARIANTS = ("mixed", "batched64_mixed", "batched64_fp64", "fp64_split_flux_ablation",
+            "ragged16_mixed")
 SAMPLE_POINTS = 2_500_000  # CPU-oracle sample: an inner region of the workload cloud
 
 
@@ -51,14 +53,17 @@ def _dist():
     return rank, world, local
 
 
-def workload_config(points_requested: int, world: int, flux_split: bool = False) -> dict:
+def workload_config(points_requested: int, world: int, flux_split: bool = False,
+                    mach: float = MACH, alpha: float = ALPHA) -> dict:
     """The `config` both arms report: the NACA 0012 cloud of about
     `points_requested` points (its exact size from the generator's grid)."""
     from paper_2108_07031_gb300 import cloud as Cl
     n_c, n_r = Cl.cloud_dims(points_requested)
     n = n_c * n_r
-    return {"workload": f"naca0012-o-cloud-{n}pts-fp64" + ("-split-flux-kernels" if flux_split else ""),
-            "points": n, "mach": MACH, "alpha_deg": ALPHA, "inner_iters": 2, "rk_stages": 4,
+    cond = "" if (mach, alpha) == (MACH, ALPHA) else f"-M{mach:g}-a{alpha:g}"
+    return {"workload": f"naca0012-o-cloud-{n}pts-fp64" + cond
+            + ("-split-flux-kernels" if flux_split else ""),
+            "points": n, "mach": mach, "alpha_deg": alpha, "inner_iters": 2, "rk_stages": 4,
             "cfl": 0.2, "parallelism": f"replicas{world}",
             "l2": "inputs larger than L2 (device working set ~17 GB), no flush",
             "initial_state": "developed: seeded smooth perturbation of the free stream at every "
@@ -190,18 +195,61 @@ def _fp64_peak():
 
 # Per-unit figures of the FP64 flux/update kernel (k_flux), from one ncu
 # capture of a stage launch on the 600,138-point cloud (8,338,298 neighbour
-# entries): 1.309e9 DFMA, 0.298e9 DADD and 0.620e9 DMUL thread instructions
-# (predicated on) = 3.54e9 FP64 flops = 424.1 flops per neighbour entry, and
-# 438.2 MB of DRAM traffic = 730.1 bytes per point. Units of one launch:
-# neighbour entries (flops) and points (bytes); both scale in proportion with
-# the cloud size. With this instruction mix a saturated FP64 pipe reaches
-# (2 DFMA + DADD + DMUL) / (2 (DFMA + DADD + DMUL)) = 0.794 of the FMA peak
-# (every FP64 instruction takes one issue slot of the pipe).
-FLUX_FP64_FLOPS_PER_NEIGHBOUR = 424.1
+# entries): 1.1095e9 DFMA, 0.2814e9 DADD and 0.6531e9 DMUL thread
+# instructions (predicated on) = 3.153e9 FP64 flops = 378.2 flops per
+# neighbour entry, and 438.2 MB of DRAM traffic = 730.1 bytes per point.
+# Units of one launch: neighbour entries (flops) and points (bytes); both
+# scale in proportion with the cloud size. With this instruction mix a
+# saturated FP64 pipe reaches (2 DFMA + DADD + DMUL) / (2 (DFMA + DADD +
+# DMUL)) = 0.771 of the FMA peak (every FP64 instruction takes one issue
+# slot of the pipe).
+FLUX_FP64_FLOPS_PER_NEIGHBOUR = 378.2
 FLUX_DRAM_BYTES_PER_POINT = 730.1
-FLUX_FRAC_CEILING = 0.794
+FLUX_FRAC_CEILING = 0.771
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # 1.2586
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 80.55: 128 FP32 lanes per SM
 ALGORITHMIC_BYTES_PER_POINT_ITERATION = 4600.0  # minimal passes, gathers from cache
+
+# The variants' dominant flux kernels, per neighbour entry (x condition) and
+# per point (x condition), from one ncu capture each of a 600,138-point
+# launch (thread-level predicated-on FP32 / FP64 instructions, DRAM bytes):
+#   mixed: k_flux_mx, FP32 flops (2 FFMA + FADD + FMUL) per entry; its FP64
+#          epilogue (state update, q-variables) is per point;
+#   split: the four k_flux_part launches and k_stage_split of one stage.
+#   mixed: 0.8738e9 FFMA + 1.1138e9 FMUL + 0.5614e9 FADD = 3.423e9 FP32 flops
+#          = 410.5 per entry (plus 57 FP64 instructions per point), 277.2 MB
+#          of DRAM traffic = 461.9 bytes per point;
+#   split: 1.5089e9 DFMA + 0.3385e9 DADD + 0.9360e9 DMUL over the five
+#          launches of a stage = 4.292e9 FP64 flops = 514.8 per entry,
+#          1354.5 MB = 2257 bytes per point.
+FLUX_MX_FP32_FLOPS_PER_NEIGHBOUR = 410.5
+FLUX_MX_DRAM_BYTES_PER_POINT = 461.9
+FLUX_SPLIT_FP64_FLOPS_PER_NEIGHBOUR = 514.8
+FLUX_SPLIT_DRAM_BYTES_PER_POINT = 2257.0
+
+
+def layout_bytes_per_point_iteration(mixed: bool, entries_per_point: float, inner: int = 2) -> float:
+    """Compulsory DRAM bytes of one iteration (4 RK stages) per point of the
+    library's device layout: every slot-major per-neighbour stream and
+    per-point record read or written once per pass, the neighbours'
+    gathered records served from cache. E = neighbour entries per point.
+      FP64  first-order sweep: (4 + 8 + 8) E + q 32 + count 4 + (q_x, q_y) 64
+            inner sweep:       (4 + 32) E + per-point sums 32 + derivatives
+                               64 in, 64 first-order, 64 out + count 4
+            flux + update:     (4 + 4 x 8) E + flag 1 + count 4 + normal 16
+                               + q 32 + derivatives 64 + U 32 in, 32 out
+                               + next q 32 + 26 (time step, U0: stage mean)
+      mixed first-order sweep: (4 + 8) E + q pair 32 + count 4 + out 32
+            inner sweep:       (4 + 8) E + coordinate pair 16 + 32 in,
+                               32 first-order, 32 out + count 4
+            flux + update:     (4 + 16) E + 1 + 4 + 16 + q pair 32
+                               + derivatives 32 + U 64 + next q 32 + 26"""
+    E = entries_per_point
+    if mixed:
+        per_stage = (12 * E + 68) + inner * (12 * E + 116) + (20 * E + 207)
+    else:
+        per_stage = (20 * E + 100) + inner * (36 * E + 228) + (36 * E + 239)
+    return 4.0 * per_stage
 
 
 def run_ours(args, rank, world, local):
@@ -220,11 +268,11 @@ def run_ours(args, rank, world, local):
     stream = torch.cuda.Stream()
     solver = L.Solver.from_cloud(cloud, flux_split=1 if args.flux_split else 0)
     solver.set_stream(stream.cuda_stream)
-    solver.set_freestream(MACH, ALPHA)
+    solver.set_freestream(args.mach, args.alpha)
     # time a developed flow: a smooth seeded perturbation of the free stream at
     # every point, so no neighbour pair has equal modified states (the flux
     # kernel skips such pairs exactly; a uniform start would time that skip)
-    solver.set_state(Cl.perturbed_state(cloud, MACH, ALPHA))
+    solver.set_state(Cl.perturbed_state(cloud, args.mach, args.alpha))
     info = solver.info()
 
     # warm-up (also captures the iteration graph)
@@ -273,9 +321,22 @@ def run_ours(args, rank, world, local):
     e2e_s = time.perf_counter() - t0
     e2e_t = max_over_ranks(e2e_s, dist)
     e2e_value = whole_job_rate(n * e2e_steps, world, e2e_t)
+    # the same, for a caller that consumes the field: the state is also read
+    # back (lskum_get_state, into pinned host memory) every step
+    out_pinned = torch.empty_like(pinned).pin_memory()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        solver.set_state_ptr(pinned.data_ptr())
+        solver.step(1)
+        _ = solver.residual_norm()
+        solver.get_state_ptr(out_pinned.data_ptr())
+    barrier()
+    e2e_state_t = max_over_ranks(time.perf_counter() - t0, dist)
+    e2e_state_value = whole_job_rate(n * e2e_steps, world, e2e_state_t)
 
     result = None
-    config = workload_config(args.points, world, args.flux_split)
+    config = workload_config(args.points, world, args.flux_split, args.mach, args.alpha)
     assert config["points"] == n
     if rank == 0:
         peaks = _fp64_peak()
@@ -307,14 +368,21 @@ def run_ours(args, rank, world, local):
                 "frac_ceiling_at_instruction_mix": FLUX_FRAC_CEILING,
                 "launch_ms": flux_launch_ms,
                 "traffic_note": "ncu dram bytes of a 0.6M-point launch scaled by points",
-                "hbm_frac_of_measured_whole_step":
-                    (ALGORITHMIC_BYTES_PER_POINT_ITERATION * n / (t_max / args.steps * 1e-3))
-                    / (mp["hbm_gbs"] * 1e9),
-                "hbm_peak_kind": mp_kind,
+                "hbm_frac_of_measured_whole_step": {
+                    "algorithmic": (ALGORITHMIC_BYTES_PER_POINT_ITERATION * n
+                                    / (t_max / args.steps * 1e-3)) / (mp["hbm_gbs"] * 1e9),
+                    "layout": (layout_bytes_per_point_iteration(False, nnz / n) * n
+                               / (t_max / args.steps * 1e-3)) / (mp["hbm_gbs"] * 1e9),
+                    "layout_bytes_per_point_iteration":
+                        layout_bytes_per_point_iteration(False, nnz / n),
+                    "peak_gbs": mp["hbm_gbs"], "peak_kind": mp_kind},
             },
             "kernel_ms": {k: {"total_ms": v[0], "launches": v[1]} for k, v in kt.items()},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n * 32,
-                    "d2h_bytes_per_step": 8, "steps": e2e_steps},
+                    "d2h_bytes_per_step": 8, "steps": e2e_steps,
+                    "with_state_readback": {"value": e2e_state_value, "unit": UNIT,
+                                            "h2d_bytes_per_step": n * 32,
+                                            "d2h_bytes_per_step": n * 32 + 8}},
             "gpu_launches": int(launches),
             "clocks": clocks,
             "cpu_baseline": cpu,
@@ -322,28 +390,39 @@ def run_ours(args, rank, world, local):
     solver.close()
     if args.variants:
         from paper_2108_07031_gb300 import cloud as Cl
-        variants = {"mixed": time_variant(args, cloud, L.MIXED, 1, stream, barrier, dist,
-                                          "10M-point cloud, one condition, block sizes autotuned",
-                                          autotune=True)}
-        c06 = _cloud(600_000)
-        mach, alpha = Cl.conditions(64)
-        variants["batched64_mixed"] = time_variant(
-            args, c06, L.MIXED, 64, stream, barrier, dist,
-            "64 seeded conditions (M ~ U[0.3,0.8], alpha ~ U[-4,6] deg) on the 600,138-point "
-            "cloud, condition-innermost, block size autotuned", conditions=(mach, alpha),
-            autotune=True)
-        variants["batched64_fp64"] = time_variant(
-            args, c06, L.FP64, 64, stream, barrier, dist,
-            "the same 64 conditions in FP64", conditions=(mach, alpha), autotune=True)
-        variants["fp64_split_flux_ablation"] = time_variant(
-            args, cloud, L.FP64, 1, stream, barrier, dist,
-            "10M-point cloud, FP64, the paper's kernel splitting (four split-flux kernels "
-            "and a stage kernel per stage)", split=True)
-        packed, sizes = _ragged_cloud()
-        variants["ragged16_mixed"] = time_variant(
-            args, packed, L.MIXED, 1, stream, barrier, dist,
-            f"16 clouds of {min(sizes)}-{max(sizes)} points packed into one launch "
-            f"({packed.n} points)", autotune=True)
+        want = set(VARIANTS) if args.variants == "all" else set(args.variants.split(","))
+        unknown = want - set(VARIANTS)
+        if unknown:
+            raise SystemExit(f"unknown variants {sorted(unknown)}; known: {', '.join(VARIANTS)}")
+        variants = {}
+        if "mixed" in want:
+            variants["mixed"] = time_variant(args, cloud, L.MIXED, 1, stream, barrier, dist,
+                                             f"{n}-point cloud, one condition, block sizes autotuned",
+                                             autotune=True)
+        if want & {"batched64_mixed", "batched64_fp64"}:
+            c06 = _cloud(600_000)
+            mach, alpha = Cl.conditions(64)
+        if "batched64_mixed" in want:
+            variants["batched64_mixed"] = time_variant(
+                args, c06, L.MIXED, 64, stream, barrier, dist,
+                "64 seeded conditions (M ~ U[0.3,0.8], alpha ~ U[-4,6] deg) on the 600,138-point "
+                "cloud, condition-innermost, block size autotuned", conditions=(mach, alpha),
+                autotune=True)
+        if "batched64_fp64" in want:
+            variants["batched64_fp64"] = time_variant(
+                args, c06, L.FP64, 64, stream, barrier, dist,
+                "the same 64 conditions in FP64", conditions=(mach, alpha), autotune=True)
+        if "fp64_split_flux_ablation" in want:
+            variants["fp64_split_flux_ablation"] = time_variant(
+                args, cloud, L.FP64, 1, stream, barrier, dist,
+                f"{n}-point cloud, FP64, the paper's kernel splitting (four split-flux kernels "
+                "and a stage kernel per stage)", split=True)
+        if "ragged16_mixed" in want:
+            packed, sizes = _ragged_cloud()
+            variants["ragged16_mixed"] = time_variant(
+                args, packed, L.MIXED, 1, stream, barrier, dist,
+                f"16 clouds of {min(sizes)}-{max(sizes)} points packed into one launch "
+                f"({packed.n} points)", autotune=True)
         if result is not None:
             for v in variants.values():
                 v["speedup_vs_fp64"] = v["value"] / value
@@ -373,8 +452,8 @@ def time_variant(args, cloud, precision, n_cond, stream, barrier, dist, what,
                             flux_split=1 if split else 0)
     s.set_stream(stream.cuda_stream)
     if conditions is None:
-        s.set_freestream(MACH, ALPHA)
-        W = Cl.perturbed_state(cloud, MACH, ALPHA)
+        s.set_freestream(args.mach, args.alpha)
+        W = Cl.perturbed_state(cloud, args.mach, args.alpha)
     else:
         s.set_conditions(*conditions)
         W = np.stack([Cl.perturbed_state(cloud, m, a) for m, a in zip(*conditions)])
@@ -401,14 +480,54 @@ def time_variant(args, cloud, precision, n_cond, stream, barrier, dist, what,
     world = dist.get_world_size() if dist is not None else 1
     t_max = max_over_ranks(ms, dist)
     value = whole_job_rate(cloud.n * n_cond * args.steps, world, t_max * 1e-3)
-    return {"workload": what, "precision": "mixed" if precision == L.MIXED else "fp64",
+    mixed = precision == L.MIXED
+    return {"workload": what, "precision": "mixed" if mixed else "fp64",
             "points": cloud.n, "conditions": n_cond, "block_size": {"flux": block[0], "q_derivatives": block[1]},
             "value": value, "unit": "point-condition-iterations/s" if n_cond > 1 else UNIT,
             "ms_per_step": t_max / args.steps, "gpu_launches": int(launches),
-            "kernel_ms": {k: {"total_ms": v[0], "launches": v[1]} for k, v in kt.items()}}
+            "kernel_ms": {k: {"total_ms": v[0], "launches": v[1]} for k, v in kt.items()},
+            "roofline": variant_roofline(mixed, split, kt["flux"], int(cloud.nbr_offsets[-1]),
+                                         cloud.n, n_cond, t_max / args.steps)}
 
 
-def inner_region(cloud, n_target: int):
+def variant_roofline(mixed: bool, split: bool, flux_time, nnz: int, n: int, n_cond: int,
+                     ms_per_step: float) -> dict:
+    """Roofline of a variant's dominant kernel (the flux kernel: FP32 issue
+    for the mixed path, the FP64 pipe otherwise) and the HBM fraction of its
+    whole step, both from the live CUDA-event times of the timed region."""
+    flux_ms, flux_n = flux_time
+    launch_s = flux_ms / max(flux_n, 1) * 1e-3
+    if mixed:
+        kernel, per_entry, per_point = ("k_flux_mx (mixed-precision flux residual + stage update)",
+                                        FLUX_MX_FP32_FLOPS_PER_NEIGHBOUR, FLUX_MX_DRAM_BYTES_PER_POINT)
+        peak, peak_src = FP32_PEAK_TFLOPS, "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz"
+    elif split:
+        kernel, per_entry, per_point = ("k_flux_part x 4 + k_stage_split (one stage, FP64)",
+                                        FLUX_SPLIT_FP64_FLOPS_PER_NEIGHBOUR,
+                                        FLUX_SPLIT_DRAM_BYTES_PER_POINT)
+        peak, peak_src = FP64_PEAK_TFLOPS, "derived: 152 SMs x 2 FP64 FMA/clk/SM x 2 flops x 2.07 GHz"
+    else:
+        kernel, per_entry, per_point = ("k_flux (flux residual + SSP-RK stage update, FP64)",
+                                        FLUX_FP64_FLOPS_PER_NEIGHBOUR, FLUX_DRAM_BYTES_PER_POINT)
+        peak, peak_src = FP64_PEAK_TFLOPS, "derived: 152 SMs x 2 FP64 FMA/clk/SM x 2 flops x 2.07 GHz"
+    achieved = per_entry * nnz * n_cond / launch_s / 1e12 if per_entry else None
+    mp, mp_kind = _peaks()
+    hbm = mp["hbm_gbs"] * 1e9
+    step_s = ms_per_step * 1e-3
+    layout = layout_bytes_per_point_iteration(mixed, nnz / n)
+    return {"kernel": kernel, "bound": "alu", "unit": "TFLOP/s", "achieved": achieved,
+            "peak": peak, "frac": achieved / peak if achieved else None, "peak_source": peak_src,
+            "launch_ms": launch_s * 1e3,
+            "traffic": per_point * n * n_cond if per_point else None,
+            "traffic_note": "ncu dram bytes of a 0.6M-point launch, scaled by points x conditions",
+            "hbm_frac_of_measured_whole_step": {
+                "algorithmic": ALGORITHMIC_BYTES_PER_POINT_ITERATION * n * n_cond / step_s / hbm,
+                "layout": layout * n * n_cond / step_s / hbm,
+                "layout_bytes_per_point_iteration": layout,
+                "peak_gbs": mp["hbm_gbs"], "peak_kind": mp_kind}}
+
+
+def inner_region(cloud, n_target: int, mach: float = MACH, alpha: float = ALPHA):
     """The inner layers of `cloud` (generator layers 0..L, L the first layer at
     which the region holds `n_target` points) as a cloud of its own, with the
     state to time on it. Stencils reach two layers out, so every point below
@@ -435,7 +554,7 @@ def inner_region(cloud, n_target: int):
     region = Cl.Cloud(xy=cloud.xy[members], normals=normals, flags=flags, nbr_offsets=new_off,
                       nbr_idx=np.concatenate(nb).astype(np.int32), n_c=cloud.n_c, n_r=L + 1,
                       k=cloud.k[members], l=cloud.l[members])
-    W = Cl.perturbed_state(cloud, MACH, ALPHA)[members]
+    W = Cl.perturbed_state(cloud, mach, alpha)[members]
     return region, W, L
 
 
@@ -443,7 +562,7 @@ def _oracle_region(args):
     """The oracle on the inner region of the workload's own cloud."""
     from oracle import oracle as O
     cloud = _cloud(args.points)
-    region, W, L = inner_region(cloud, SAMPLE_POINTS)
+    region, W, L = inner_region(cloud, SAMPLE_POINTS, args.mach, args.alpha)
     return O, O.OracleCloud.from_cloud(region), W, region.n, L, cloud.n
 
 
@@ -486,7 +605,7 @@ def run_reference(args, rank, world):
         "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "impl": "reference",
-        "config": workload_config(args.points, world),
+        "config": workload_config(args.points, world, mach=args.mach, alpha=args.alpha),
         "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": cores,
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -500,11 +619,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--points", type=int, default=WORKLOAD_POINTS)
+    ap.add_argument("--mach", type=float, default=MACH)
+    ap.add_argument("--alpha", type=float, default=ALPHA, help="angle of attack, degrees")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--flux-split", action="store_true",
                     help="run the headline with the split flux kernels (profiling the ablation)")
-    ap.add_argument("--no-variants", dest="variants", action="store_false",
-                    help="skip the mixed-precision variant line")
+    ap.add_argument("--variants", default="all",
+                    help="comma-separated variants to time after the headline (default all: "
+                         + ", ".join(VARIANTS) + ")")
+    ap.add_argument("--no-variants", dest="variants", action="store_const", const="",
+                    help="time the headline only")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)  # at least three untimed warm-up steps
     args.steps = max(args.steps, 1)

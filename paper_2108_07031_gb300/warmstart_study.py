@@ -52,6 +52,8 @@ def main():
                          "position harmonics (surrogate.wall_features)")
     ap.add_argument("--data-cache", default="",
                     help="file (.npy) to keep the converged training states in between runs")
+    ap.add_argument("--save-states", default="",
+                    help="file (.npz) for the held-out conditions' final states of both starts")
     args = ap.parse_args()
     prec = L.MIXED if args.precision == "mixed" else L.FP64
     log = lambda m: print(m, flush=True)  # noqa: E731
@@ -150,6 +152,9 @@ def main():
         "dcd_abs_mean": float(np.mean(np.abs(results["warm"]["cd"] - results["cold"]["cd"]))),
         "dcl_abs_max": float(np.max(np.abs(results["warm"]["cl"] - results["cold"]["cl"]))),
         "dcd_abs_max": float(np.max(np.abs(results["warm"]["cd"] - results["cold"]["cd"]))),
+        "residue_first_cold": r_first.tolist(),
+        "residue_after_100_cold": results["cold"]["hist"][0].tolist(),
+        "residue_after_100_warm": results["warm"]["hist"][0].tolist(),
         "residue_end_cold": results["cold"]["hist"][-1].tolist(),
         "residue_end_warm": results["warm"]["hist"][-1].tolist(),
         "eval_iters": args.eval_iters,
@@ -158,6 +163,9 @@ def main():
     }
     with open(args.out, "w") as f:
         json.dump(out, f, indent=1)
+    if args.save_states:
+        np.savez(args.save_states, cold=results["cold"]["W"], warm=results["warm"]["W"],
+                 mach=m_te, alpha=a_te)
     log(json.dumps({k: v for k, v in out.items() if not isinstance(v, list)}))
 
 
