@@ -11,8 +11,9 @@
  * Network: 21 input features (zero-padded to LSKUM_MLP_IN_PADDED) -> five
  * hidden layers of LSKUM_MLP_WIDTH (tanh) -> LSKUM_MLP_OUT linear outputs
  * (six linear layers). Training and inference run in hand-written CUDA
- * kernels: BF16 tensor-core GEMMs (mma.sync m16n8k16) accumulating in FP32,
- * FP32 master weights, Adam.
+ * kernels: BF16 tensor-core GEMMs (mma.sync m16n8k16, or tcgen05 for the
+ * forward pass of the 256-wide layers, see lskum_mlp_set_gemm) accumulating
+ * in FP32, FP32 master weights, Adam.
  *
  * Parameters (flat FP32, host order): for l = 0..5: W_l [out_l x in_l]
  * row-major, then b_l [out_l]; in_0 = LSKUM_MLP_IN_PADDED (columns 21..31
@@ -82,6 +83,22 @@ int lskum_mlp_train_step(lskum_mlp* h, const float* feat_dev, const float* targe
 
 /* Waits for the handle's stream. */
 int lskum_mlp_sync(lskum_mlp* h);
+
+/* GEMM path of the forward pass's five 256-wide layers:
+ *   LSKUM_MLP_GEMM_MMA_SYNC  warp-level mma.sync m16n8k16 (the default);
+ *   LSKUM_MLP_GEMM_TCGEN05   fifth-generation tensor cores: one CTA per 128
+ *     rows stages its X tile and W in shared memory, one thread issues
+ *     tcgen05.mma (M 128, N 256, K 16) into a tensor-memory accumulator,
+ *     the epilogue reads it back with tcgen05.ld (sm_100-family GPUs only).
+ * Both accumulate BF16 products in FP32; results agree to the order of the
+ * FP32 sums. The backward pass and the 4-wide output layer use mma.sync.
+ * With tcgen05, a synchronising call returns LSKUM_ERR_TIMEOUT if a GEMM
+ * gave up waiting for its accumulators (a bounded wait; the context stays
+ * usable). Waits for the handle's stream first. Errors: INVALID_ARG
+ * (unknown path). No counterpart in the paper. */
+#define LSKUM_MLP_GEMM_MMA_SYNC 0
+#define LSKUM_MLP_GEMM_TCGEN05 1
+int lskum_mlp_set_gemm(lskum_mlp* h, int path);
 
 /* Runs the handle's work on the caller's CUDA stream (a cudaStream_t; NULL
  * restores the handle's own stream). Work the caller queues on the same

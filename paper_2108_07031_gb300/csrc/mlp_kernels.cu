@@ -328,6 +328,207 @@ __global__ void __launch_bounds__(256) k_gemm_bf16_tc(const __nv_bfloat16* __res
             }
 }
 
+// ------------------------------------------------- tcgen05 forward GEMM
+// Z = X W^T + b (tanh or linear epilogue) of a hidden layer (256 outputs) on
+// the fifth-generation tensor cores. One CTA of eight warps per 128-row tile
+// of X and 128-column half of the outputs: it stages X[m0:m0+128, 0:K] and
+// W[n0:n0+128, 0:K] (K <= 256: at most 2 x 64 KB) in shared memory with
+// cp.async in K stages of 64 (one copy group each), and as each stage lands
+// one thread issues its four tcgen05.mma (M 128, N 128, K 16, BF16 x BF16 ->
+// FP32) into a 128-column accumulator in tensor memory, so the MMAs of a
+// stage overlap the copies of the next; the last commit arrives on an
+// mbarrier, and each warp reads a 32-lane x 64-column quarter of the
+// accumulator back with tcgen05.ld for the epilogue (warp w: lanes 32 (w mod
+// 4) .., columns 64 (w div 4) ..).
+//
+// Shared-memory operand layout: the no-swizzle K-major canonical form of the
+// matrix descriptors: core matrices of 8 rows x 16 bytes (8 BF16 along K)
+// stored as 128 contiguous bytes; core matrix (r/8, k/8) of an operand at
+// byte (r/8) SBO + (k/8) LBO with LBO = 128 (next core matrix along K) and
+// SBO = 16 K (next 8-row group). One MMA reads two core matrices along K, so
+// consecutive MMAs advance both descriptors' start by 256 bytes.
+constexpr int kUmmaM = 128, kUmmaN = 128, kUmmaK = 16, kUmmaStageK = 64, kUmmaThreads = 256;
+constexpr int kUmmaOut = 256;  // outputs of a hidden layer (two CTAs' halves)
+
+__host__ __device__ constexpr size_t umma_smem_bytes(int K) {
+    return size_t(kUmmaM + kUmmaN) * size_t(K) * 2 + 16;  // A, B, mbarrier, TMEM address
+}
+
+// SM100 shared-memory matrix descriptor: bits [0,14) start address >> 4,
+// [16,30) leading-dimension byte offset >> 4, [32,46) stride-dimension byte
+// offset >> 4, [46,48) descriptor version 1, [61,64) layout 0 (no swizzle).
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return uint64_t((saddr >> 4) & 0x3FFFu) | (uint64_t((lbo >> 4) & 0x3FFFu) << 16) |
+           (uint64_t((sbo >> 4) & 0x3FFFu) << 32) | (uint64_t(1) << 46);
+}
+
+// Instruction descriptor of kind::f16: D FP32 (bits [4,6) = 1), A and B BF16
+// (bits [7,10) and [10,13) = 1), both K-major (bits 15, 16 = 0), N >> 3 at
+// bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t umma_idesc_bf16_f32(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
+}
+
+// Waits for phase `parity` of the mbarrier at shared address `bar`, polling
+// at most `limit` times (with a short sleep between polls); false when the
+// limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int limit) {
+    for (int i = 0; i < limit; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            "selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        __nanosleep(128);
+    }
+    return false;
+}
+
+// tcgen05.ld of 32 consecutive FP32 accumulator columns of this thread's
+// tensor-memory lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+        "%28, %29, %30, %31}, [%32];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// X: M x K BF16 row-major (K a multiple of 16, K <= 256, rows 16-byte
+// aligned), W: 256 x K BF16 row-major, bias[256]; outputs row-major with 256
+// columns: EPI kBiasTanh writes Cf = tanh(Z) and Cb = bf16(Cf), kBiasLinear
+// Cf = Z. Grid (M / 128 rounded up, 2). `err` receives 1 if the accumulator
+// wait ran out (the tile's outputs are then not written).
+__device__ __forceinline__ void cp_async_wait_dyn(int n) {  // n in 0..3 groups may stay in flight
+    if (n <= 0) cp_async_wait<0>();
+    else if (n == 1) cp_async_wait<1>();
+    else if (n == 2) cp_async_wait<2>();
+    else cp_async_wait<3>();
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(kUmmaThreads, 1) k_gemm_fwd_umma(const __nv_bfloat16* __restrict__ X,
+                                                                   int M, int K,
+                                                                   const __nv_bfloat16* __restrict__ W,
+                                                                   const float* __restrict__ bias,
+                                                                   float* __restrict__ Cf,
+                                                                   __nv_bfloat16* __restrict__ Cb,
+                                                                   int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * kUmmaM, n0 = blockIdx.y * kUmmaN;
+    const uint32_t sA = smem_u32(smem);
+    const uint32_t sB = sA + uint32_t(kUmmaM * K * 2);
+    const uint32_t bar = sB + uint32_t(kUmmaN * K * 2);
+    const uint32_t tslot = bar + 8;
+    const uint32_t sbo = uint32_t(K) * 16;  // bytes between 8-row groups
+    const int kc = K / 8;                   // 16-byte chunks per row
+    const int nst = (K + kUmmaStageK - 1) / kUmmaStageK;  // 1..4 stages
+
+    // every stage's copies up front, one group per stage: chunk c of row r
+    // lands in core matrix (r/8, c)
+    for (int st = 0; st < nst; ++st) {
+        const int c0 = st * (kUmmaStageK / 8), c1 = min(kc, c0 + kUmmaStageK / 8), w = c1 - c0;
+        for (int i = tid; i < kUmmaM * w; i += kUmmaThreads) {
+            const int r = i / w, c = c0 + (i - r * w), gm = m0 + r;
+            const bool ok = gm < M;
+            cp_async16(sA + uint32_t(r >> 3) * sbo + uint32_t(c) * 128 + uint32_t(r & 7) * 16,
+                       ok ? X + int64_t(gm) * K + c * 8 : X, ok);
+        }
+        for (int i = tid; i < kUmmaN * w; i += kUmmaThreads) {
+            const int r = i / w, c = c0 + (i - r * w);
+            cp_async16(sB + uint32_t(r >> 3) * sbo + uint32_t(c) * 128 + uint32_t(r & 7) * 16,
+                       W + int64_t(n0 + r) * K + c * 8, true);
+        }
+        cp_async_commit();
+    }
+    if (warp == 0) {  // 128 columns x 128 lanes of 32-bit accumulators
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(tslot),
+                     "r"(kUmmaN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar));
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    uint32_t tmem = 0;
+    constexpr uint32_t idesc = umma_idesc_bf16_f32(kUmmaM, kUmmaN);
+    for (int st = 0; st < nst; ++st) {
+        cp_async_wait_dyn(nst - 1 - st);  // this thread's copies of stages 0..st have landed
+        // the staged operands become visible to the tensor cores (async proxy)
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        __syncthreads();  // ... everyone's
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        if (st == 0) asm volatile("ld.shared.u32 %0, [%1];\n" : "=r"(tmem) : "r"(tslot));
+        if (tid == 0) {
+            const int k1 = min(K, (st + 1) * kUmmaStageK) / kUmmaK;
+            for (int ks = st * (kUmmaStageK / kUmmaK); ks < k1; ++ks) {
+                const uint64_t da = umma_desc(sA + uint32_t(ks) * 256, 128, sbo);
+                const uint64_t db = umma_desc(sB + uint32_t(ks) * 256, 128, sbo);
+                asm volatile(
+                    "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(da), "l"(db), "r"(idesc), "r"(ks));
+            }
+            if (st == nst - 1)
+                asm volatile(
+                    "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
+                    : "memory");
+        }
+    }
+    // the accumulators are complete when the mbarrier's phase 0 completes
+    // (microseconds; the limit, ~0.5 s, only ends a wait that would not)
+    const bool done = __all_sync(0xffffffffu, mbar_wait(bar, 0, 1 << 22));
+    if (!done && lane == 0) atomicExch(err, 1);
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (done) {
+        const int q = warp & 3, h = warp >> 2;
+        const int m = m0 + q * 32 + lane;  // this thread's row = its tensor-memory lane
+        for (int cc = 0; cc < kUmmaN / 2; cc += 32) {
+            const int c0 = h * (kUmmaN / 2) + cc;  // column within this CTA's half
+            float v[32];
+            tmem_ld32(tmem + (uint32_t(q * 32) << 16) + uint32_t(c0), v);
+            if (m < M) {
+                const int n = n0 + c0;
+                float4* of = reinterpret_cast<float4*>(Cf + int64_t(m) * kUmmaOut + n);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    float4 o;
+                    o.x = v[4 * j] + __ldg(bias + n + 4 * j);
+                    o.y = v[4 * j + 1] + __ldg(bias + n + 4 * j + 1);
+                    o.z = v[4 * j + 2] + __ldg(bias + n + 4 * j + 2);
+                    o.w = v[4 * j + 3] + __ldg(bias + n + 4 * j + 3);
+                    if (EPI == kBiasTanh) {
+                        o.x = tanhf(o.x); o.y = tanhf(o.y); o.z = tanhf(o.z); o.w = tanhf(o.w);
+                        __nv_bfloat162* ob =
+                            reinterpret_cast<__nv_bfloat162*>(Cb + int64_t(m) * kUmmaOut + n + 4 * j);
+                        ob[0] = __floats2bfloat162_rn(o.x, o.y);
+                        ob[1] = __floats2bfloat162_rn(o.z, o.w);
+                    }
+                    of[j] = o;
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kUmmaN));
+}
+
 // Features: per sample raw (x, y, wall distance, M, alpha_deg) ->
 // [x/10, y/10, log(d + 1e-3)/5, (M - 0.55)/0.25, (alpha - 1)/5,
 //  sin(P (x, y)), cos(P (x, y)) (8 projections each), 0 x 11 padding],
@@ -485,6 +686,8 @@ struct lskum_mlp {
     __nv_bfloat16* dZb = nullptr;
     double* partial = nullptr;
     double* loss_dev = nullptr;
+    int gemm_path = LSKUM_MLP_GEMM_MMA_SYNC;
+    int* err_dev = nullptr;  // set by a tcgen05 GEMM whose accumulator wait ran out
     std::vector<void*> allocs;
 };
 
@@ -542,6 +745,38 @@ cudaError_t launch_tc(lskum_mlp* h, dim3 grid, const __nv_bfloat16* A, int64_t s
     k_gemm_bf16_tc<EPI, AK, BK><<<grid, 256, smem, h->stream>>>(A, sam, sak, B, sbk, sbn, M, N, K, bias,
                                                                 Cf, Cb, ldc, kchunk);
     return cudaGetLastError();
+}
+
+// The tcgen05 forward GEMM's requirements: 256 outputs, K a multiple of 16 up
+// to 256 (16-byte rows), 16-byte aligned operands.
+bool umma_ok(const void* X, const void* W, int N, int K) {
+    return N == kUmmaOut && K % kUmmaK == 0 && K >= kUmmaK && K <= 256 &&
+           !(reinterpret_cast<uintptr_t>(X) & 15) && !(reinterpret_cast<uintptr_t>(W) & 15);
+}
+
+template <int EPI>
+cudaError_t launch_umma(lskum_mlp* h, const __nv_bfloat16* X, int M, int K, const __nv_bfloat16* W,
+                        const float* bias, float* Cf, __nv_bfloat16* Cb) {
+    // at least 60 KB, so at most three CTAs share an SM: their 128-column
+    // accumulators fit its 512 tensor-memory columns and no allocation waits
+    const size_t smem = std::max<size_t>(umma_smem_bytes(K), 60 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_fwd_umma<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(umma_smem_bytes(256)));
+    if (e != cudaSuccess) return e;
+    const dim3 grid(blocks(M, kUmmaM), kUmmaOut / kUmmaN);
+    k_gemm_fwd_umma<EPI><<<grid, kUmmaThreads, smem, h->stream>>>(X, M, K, W, bias, Cf, Cb, h->err_dev);
+    return cudaGetLastError();
+}
+
+// After a synchronising call: LSKUM_ERR_TIMEOUT (and the flag cleared) if a
+// tcgen05 GEMM gave up waiting for its accumulators.
+int check_gemm_status(lskum_mlp* h) {
+    if (h->gemm_path != LSKUM_MLP_GEMM_TCGEN05) return LSKUM_OK;
+    int flag = 0;
+    MLP_CUDA(cudaMemcpy(&flag, h->err_dev, sizeof(int), cudaMemcpyDeviceToHost));
+    if (!flag) return LSKUM_OK;
+    MLP_CUDA(cudaMemset(h->err_dev, 0, sizeof(int)));
+    return fail(LSKUM_ERR_TIMEOUT, "tcgen05 GEMM: accumulator wait ran out");
 }
 
 template <int EPI>
@@ -602,7 +837,9 @@ int forward(lskum_mlp* h, int64_t n) {
         const int K = layer_in(l), N = layer_out(l);
         const float* b = h->p + h->L.b_off[l];
         cudaError_t e;
-        if (l < kLayers - 1)
+        if (l < kLayers - 1 && h->gemm_path == LSKUM_MLP_GEMM_TCGEN05 && umma_ok(h->Ab[l], h->L.W[l], N, K))
+            e = launch_umma<kBiasTanh>(h, h->Ab[l], int(n), K, h->L.W[l], b, h->Af[l + 1], h->Ab[l + 1]);
+        else if (l < kLayers - 1)
             e = gemm<kBiasTanh>(h, h->Ab[l], K, 1, h->L.W[l], 1, K, int(n), N, K, b, h->Af[l + 1],
                                 h->Ab[l + 1], N);
         else
@@ -689,7 +926,9 @@ int lskum_mlp_create(int64_t capacity, const float* proj, lskum_mlp** out) {
         (e = alloc(h, &h->dZb, capacity * kWidth)) != cudaSuccess ||
         (e = alloc(h, &h->slices, int64_t(kMaxSlices) * kWidth * kWidth)) != cudaSuccess ||
         (e = alloc(h, &h->partial, int64_t(blocks(capacity * kOut, 256)))) != cudaSuccess ||
-        (e = alloc(h, &h->loss_dev, 1)) != cudaSuccess)
+        (e = alloc(h, &h->loss_dev, 1)) != cudaSuccess ||
+        (e = alloc(h, &h->err_dev, 1)) != cudaSuccess ||
+        (e = cudaMemset(h->err_dev, 0, sizeof(int))) != cudaSuccess)
         return bail(e);
     for (int l = 0; l <= kLayers; ++l) {
         const int w = l == 0 ? kIn : (l == kLayers ? kOut : kWidth);
@@ -750,7 +989,7 @@ int lskum_mlp_predict(lskum_mlp* h, const float* feat, int64_t n, float* out) {
     if (rc) return rc;
     MLP_CUDA(cudaMemcpyAsync(out, h->Af[kLayers], sizeof(float) * n * kOut, cudaMemcpyDeviceToDevice, h->stream));
     MLP_CUDA(cudaStreamSynchronize(h->stream));
-    return LSKUM_OK;
+    return check_gemm_status(h);
 }
 
 int lskum_mlp_gradients(lskum_mlp* h, const float* feat, const float* target, int64_t n, float* grads,
@@ -763,7 +1002,7 @@ int lskum_mlp_gradients(lskum_mlp* h, const float* feat, const float* target, in
     if (grads) MLP_CUDA(cudaMemcpyAsync(grads, h->g, sizeof(float) * h->nparam, cudaMemcpyDeviceToHost, h->stream));
     if (loss) MLP_CUDA(cudaMemcpyAsync(loss, h->loss_dev, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     MLP_CUDA(cudaStreamSynchronize(h->stream));
-    return LSKUM_OK;
+    return check_gemm_status(h);
 }
 
 int lskum_mlp_train_step(lskum_mlp* h, const float* feat, const float* target, int64_t n, float lr,
@@ -785,6 +1024,7 @@ int lskum_mlp_train_step(lskum_mlp* h, const float* feat, const float* target, i
     if (loss) {
         MLP_CUDA(cudaMemcpyAsync(loss, h->loss_dev, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
         MLP_CUDA(cudaStreamSynchronize(h->stream));
+        return check_gemm_status(h);
     }
     return LSKUM_OK;
 }
@@ -792,6 +1032,14 @@ int lskum_mlp_train_step(lskum_mlp* h, const float* feat, const float* target, i
 int lskum_mlp_sync(lskum_mlp* h) {
     if (!h) return fail(LSKUM_ERR_INVALID_ARG, "null");
     MLP_CUDA(cudaStreamSynchronize(h->stream));
+    return check_gemm_status(h);
+}
+
+int lskum_mlp_set_gemm(lskum_mlp* h, int path) {
+    if (!h || (path != LSKUM_MLP_GEMM_MMA_SYNC && path != LSKUM_MLP_GEMM_TCGEN05))
+        return fail(LSKUM_ERR_INVALID_ARG, "lskum_mlp_set_gemm: unknown path");
+    MLP_CUDA(cudaStreamSynchronize(h->stream));
+    h->gemm_path = path;
     return LSKUM_OK;
 }
 

@@ -44,6 +44,7 @@ def _lib():
             "lskum_mlp_train_step": ([P, P, P, I64, F, P], I),
             "lskum_mlp_sync": ([P], I),
             "lskum_mlp_set_stream": ([P, P], I),
+            "lskum_mlp_set_gemm": ([P, I], I),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -56,7 +57,9 @@ def _lib():
 EXPORTED = ("lskum_mlp_num_params", "lskum_mlp_create", "lskum_mlp_destroy",
             "lskum_mlp_set_params", "lskum_mlp_get_params", "lskum_mlp_features",
             "lskum_mlp_predict", "lskum_mlp_gradients", "lskum_mlp_train_step", "lskum_mlp_sync",
-            "lskum_mlp_set_stream")
+            "lskum_mlp_set_stream", "lskum_mlp_set_gemm")
+
+GEMM_MMA_SYNC, GEMM_TCGEN05 = 0, 1
 
 
 def projection(seed: int = 2108, scales=(1.0,) * 8) -> np.ndarray:
@@ -111,6 +114,11 @@ class MLP:
         default stream, is passed as cudaStreamLegacy)."""
         h = int(handle) if handle else 1  # 1 == cudaStreamLegacy
         L._check(self._lib.lskum_mlp_set_stream(self._h, C.c_void_p(h)), "lskum_mlp_set_stream")
+
+    def set_gemm(self, path: int):
+        """GEMM path of the forward pass's 256-wide layers (GEMM_MMA_SYNC or
+        GEMM_TCGEN05)."""
+        L._check(self._lib.lskum_mlp_set_gemm(self._h, int(path)), "lskum_mlp_set_gemm")
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

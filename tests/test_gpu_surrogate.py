@@ -72,6 +72,44 @@ def test_forward_and_gradients_match_reference(net, n):
             off += size
 
 
+@pytest.mark.parametrize("n", [4096, 1000, 333, 40])
+def test_tcgen05_forward_matches_reference(net, n):
+    """The forward pass with its 256-wide layers on tcgen05 (tensor-memory
+    accumulators, 128-row tiles; ragged batches fill the last tile with zero
+    rows): outputs against the FP64 reference with the same BF16 rounding
+    points (5e-3 norm-wise) and against the mma.sync path (the two sum the
+    same FP32 products in another order: 1e-2 of the output's scale, where a
+    hidden activation's BF16 rounding may flip between them); gradients with
+    it to the reference's 2e-2 per layer."""
+    feat, T = _batch(n, 4)
+    p = S.init_params(5)
+    p[-4:] = [0.1, -0.2, 0.05, 0.3]
+    net.set_params(p)
+    fd, Td = torch.from_numpy(feat).cuda(), torch.from_numpy(T).cuda()
+    try:
+        net.set_gemm(S.GEMM_MMA_SYNC)
+        Y_ref = net.predict(fd).cpu().numpy()
+        net.set_gemm(S.GEMM_TCGEN05)
+        Y = net.predict(fd).cpu().numpy()
+        Y2 = net.predict(fd).cpu().numpy()
+        loss, g = net.gradients(fd, Td)
+    finally:
+        net.set_gemm(S.GEMM_MMA_SYNC)
+    assert np.array_equal(Y, Y2)  # deterministic
+    Y_o, _ = M.forward(p, feat, emulate=True)
+    print(f"n {n}: tcgen05 vs reference {normwise(Y, Y_o):.2e}, vs mma.sync {normwise(Y, Y_ref):.2e}")
+    assert normwise(Y, Y_o) < 5e-3
+    assert normwise(Y, Y_ref) < 1e-2
+    loss_o, g_o = M.loss_and_grad(p, feat, T, emulate=True)
+    assert abs(loss - loss_o) < 1e-3 * loss_o
+    off = 0
+    for nn_, k in M.layer_shapes():
+        for size in (nn_ * k, nn_):
+            gl, gol = g[off:off + size], g_o[off:off + size]
+            assert np.abs(gl - gol).max() <= 2e-2 * np.abs(gol).max() + 1e-9, (nn_, k, size)
+            off += size
+
+
 def test_training_reduces_loss(net):
     """Adam on a smooth target of the features: loss falls by 10x in 300 steps."""
     rng = np.random.Generator(np.random.PCG64(5))
