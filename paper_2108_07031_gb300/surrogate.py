@@ -334,3 +334,37 @@ def predict_state(mlp: MLP, cloud, wall_d, mach, alpha_deg, arc=None):
     W[wall, 1] -= un * n[:, 0]
     W[wall, 2] -= un * n[:, 1]
     return W
+
+
+def _time_predict(batches, repeats):
+    """Host-timed predict of random feature batches with each forward GEMM path."""
+    import time
+
+    import torch
+    net = MLP(capacity=max(batches), seed=1)
+    try:
+        for n in batches:
+            fd = torch.randn(n, 32, device="cuda")
+            fd[:, 21:] = 0
+            for path, name in ((GEMM_MMA_SYNC, "mma.sync"), (GEMM_TCGEN05, "tcgen05")):
+                net.set_gemm(path)
+                net.predict(fd)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                for _ in range(repeats):
+                    net.predict(fd)
+                torch.cuda.synchronize()
+                print(f"batch {n}, {name}: predict {(time.perf_counter() - t0) / repeats * 1e6:.1f} us",
+                      flush=True)
+    finally:
+        net.set_gemm(GEMM_MMA_SYNC)
+        net.close()
+
+
+if __name__ == "__main__":
+    import argparse
+    ap = argparse.ArgumentParser(description="time the surrogate's predict with both GEMM paths")
+    ap.add_argument("--batches", default="4096", help="comma-separated batch sizes")
+    ap.add_argument("--repeats", type=int, default=50)
+    a = ap.parse_args()
+    _time_predict([int(v) for v in a.batches.split(",")], a.repeats)
