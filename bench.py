@@ -204,6 +204,7 @@ def _fp64_peak():
 # DMUL)) = 0.771 of the FMA peak (every FP64 instruction takes one issue
 # slot of the pipe).
 FLUX_FP64_FLOPS_PER_NEIGHBOUR = 378.2
+FLUX_FP64_INSTR_PER_NEIGHBOUR = 245.1  # DFMA + DADD + DMUL
 FLUX_DRAM_BYTES_PER_POINT = 730.1
 FLUX_FRAC_CEILING = 0.771
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # 1.2586
@@ -366,6 +367,10 @@ def run_ours(args, rank, world, local):
                 "measured_fma_peak_source": "pure-DFMA probe (pipe_peaks) run live on this GPU",
                 "flops_per_launch": FLUX_FP64_FLOPS_PER_NEIGHBOUR * nnz,
                 "frac_ceiling_at_instruction_mix": FLUX_FRAC_CEILING,
+                # the pipe's own bound: FP64 instructions issued per second
+                # against 152 SMs x 2 per clock x 2.07 GHz
+                "fp64_issue_frac": (FLUX_FP64_INSTR_PER_NEIGHBOUR * nnz / (flux_launch_ms * 1e-3))
+                                   / (FP64_PEAK_TFLOPS * 1e12 / 2) if flux_launch_ms else None,
                 "launch_ms": flux_launch_ms,
                 "traffic_note": "ncu dram bytes of a 0.6M-point launch scaled by points",
                 "hbm_frac_of_measured_whole_step": {

@@ -24,6 +24,7 @@ ERRORS = {
     -1: "INVALID_ARG", -2: "BAD_CONNECTIVITY", -3: "DEGENERATE_STENCIL", -4: "CUDA",
     -5: "DIVERGED", -6: "TIMEOUT", -7: "STATE",
 }
+ERR_DIVERGED = -5
 
 INTERIOR, WALL, OUTER = 0, 1, 2
 OUTER_KINETIC, OUTER_FREESTREAM = 0, 1

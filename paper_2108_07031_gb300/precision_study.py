@@ -1,12 +1,15 @@
 """Mixed precision against FP64 on large clouds.
 
   python -m paper_2108_07031_gb300.precision_study --points 10000000 --iters 200 \
-      [--mach 0.85 --alpha 1.0] [--out precision_study.json]
+      [--mach 0.85 --alpha 1.0] [--cfl 0.2] [--out precision_study.json]
 
 Runs the same iterations from the free stream in both precisions on one
 NACA 0012 cloud (shuffled input order, the benchmark's family) and reports
 the lift and drag of both, the norm-wise state difference, the residue
-histories and the time per iteration of each. The FP64 path is the one the
+histories and the time per iteration of each. If the state turns
+non-physical (the solver's DIVERGED status), the run stops, records the
+iteration window, and the comparison uses the last state snapshot before it
+(the same iteration in both precisions, checked). The FP64 path is the one the
 parity tests hold to the FP64 CPU oracle; at these sizes the oracle itself
 would need hours per thousand iterations.
 """
@@ -20,31 +23,47 @@ import time
 import numpy as np
 
 
-def _run(cloud, precision, mach, alpha, iters, chunk):
+def _run(cloud, precision, mach, alpha, iters, chunk, cfl, snapshot_every):
+    """Runs `iters` iterations from the free stream. Returns the forces, the
+    residue history, the time per iteration and the state at the last
+    snapshot (every `snapshot_every` chunks, and at the end); if the state
+    turns non-physical, the iteration window where it did and the last
+    snapshot before it."""
     import torch
 
     from . import lskum as L
     t0 = time.perf_counter()
-    with L.Solver.from_cloud(cloud, precision=precision) as s:
+    with L.Solver.from_cloud(cloud, precision=precision, cfl=cfl) as s:
         t_create = time.perf_counter() - t0
         s.set_freestream(mach, alpha)
         s.step(2)  # warm-up: builds the iteration graph
         s.set_freestream(mach, alpha)
         torch.cuda.synchronize()
         hist, t_iter = [], 0.0
-        done = 0
+        done, n_chunk, diverged = 0, 0, None
+        snap = {"iteration": 0, "W": s.get_state(), "cl": 0.0, "cd": 0.0}
         while done < iters:
             k = min(chunk, iters - done)
             t0 = time.perf_counter()
-            s.step(k)
+            try:
+                s.step(k)
+            except L.LskumError as e:
+                if e.code != L.ERR_DIVERGED:
+                    raise
+                diverged = [done, done + k]
+                break
             r = s.residual_norm()
             t_iter += time.perf_counter() - t0
             done += k
+            n_chunk += 1
             hist.append((done, r))
-        cl, cd = s.forces()
-        W = s.get_state()
-    return {"cl": cl, "cd": cd, "hist": hist, "seconds_per_iteration": t_iter / iters,
-            "create_seconds": t_create}, W
+            if n_chunk % snapshot_every == 0 or done == iters:
+                cl, cd = s.forces()
+                snap = {"iteration": done, "W": s.get_state(), "cl": cl, "cd": cd}
+    out = {"cl": snap["cl"], "cd": snap["cd"], "compared_iteration": snap["iteration"],
+           "hist": hist, "seconds_per_iteration": t_iter / max(done, 1),
+           "create_seconds": t_create, "diverged_between": diverged}
+    return out, snap["W"]
 
 
 def main():
@@ -55,8 +74,12 @@ def main():
     ap.add_argument("--points", type=int, default=10_000_000)
     ap.add_argument("--iters", type=int, default=200)
     ap.add_argument("--chunk", type=int, default=50)
+    ap.add_argument("--snapshot-every", type=int, default=1,
+                    help="chunks between state snapshots (the comparison falls back to the "
+                         "last one if the state turns non-physical)")
     ap.add_argument("--mach", type=float, default=0.85)
     ap.add_argument("--alpha", type=float, default=1.0)
+    ap.add_argument("--cfl", type=float, default=0.2)
     ap.add_argument("--out", default="precision_study.json")
     args = ap.parse_args()
 
@@ -65,16 +88,25 @@ def main():
     cloud = Cl.naca0012_cloud(n_c, n_r, shuffle=True)
     t_cloud = time.perf_counter() - t0
     out = {"points": cloud.n, "n_c": n_c, "n_r": n_r, "mach": args.mach, "alpha_deg": args.alpha,
-           "iterations": args.iters, "cloud_seconds": t_cloud}
-    r64, W64 = _run(cloud, L.FP64, args.mach, args.alpha, args.iters, args.chunk)
-    rmx, Wmx = _run(cloud, L.MIXED, args.mach, args.alpha, args.iters, args.chunk)
+           "iterations": args.iters, "cfl": args.cfl, "cloud_seconds": t_cloud}
+    r64, W64 = _run(cloud, L.FP64, args.mach, args.alpha, args.iters, args.chunk, args.cfl,
+                    args.snapshot_every)
+    rmx, Wmx = _run(cloud, L.MIXED, args.mach, args.alpha, args.iters, args.chunk, args.cfl,
+                    args.snapshot_every)
     scale = np.abs(W64).max(axis=0)
     out["fp64"] = r64
     out["mixed"] = rmx
     out["state_normwise_diff"] = float((np.abs(Wmx - W64).max(axis=0) / scale).max())
     out["dcl"] = abs(rmx["cl"] - r64["cl"])
     out["dcd"] = abs(rmx["cd"] - r64["cd"])
-    out["residue_rel_diff_last"] = abs(rmx["hist"][-1][1] - r64["hist"][-1][1]) / r64["hist"][-1][1]
+    if r64["compared_iteration"] != rmx["compared_iteration"]:
+        raise RuntimeError("the two precisions stopped at different iterations: "
+                           f"{r64['diverged_between']} vs {rmx['diverged_between']}")
+    h64 = dict(r64["hist"])
+    hmx = dict(rmx["hist"])
+    it = r64["compared_iteration"]
+    out["compared_iteration"] = it
+    out["residue_rel_diff_at_compared"] = abs(hmx[it] - h64[it]) / h64[it] if it in h64 else None
     out["speedup_mixed"] = r64["seconds_per_iteration"] / rmx["seconds_per_iteration"]
     out["mixed_point_iterations_per_s"] = cloud.n / rmx["seconds_per_iteration"]
     out["fp64_point_iterations_per_s"] = cloud.n / r64["seconds_per_iteration"]
