@@ -1,7 +1,7 @@
 """Mixed precision against FP64 on large clouds.
 
   python -m paper_2108_07031_gb300.precision_study --points 10000000 --iters 200 \
-      [--mach 0.85 --alpha 1.0] [--cfl 0.2] [--out precision_study.json]
+      [--mach 0.85 --alpha 1.0] [--cfl 0.2] [--option wall_factor=1] [--out precision_study.json]
 
 Runs the same iterations from the free stream in both precisions on one
 NACA 0012 cloud (shuffled input order, the benchmark's family) and reports
@@ -23,7 +23,7 @@ import time
 import numpy as np
 
 
-def _run(cloud, precision, mach, alpha, iters, chunk, cfl, snapshot_every):
+def _run(cloud, precision, mach, alpha, iters, chunk, cfl, snapshot_every, options):
     """Runs `iters` iterations from the free stream. Returns the forces, the
     residue history, the time per iteration and the state at the last
     snapshot (every `snapshot_every` chunks, and at the end); if the state
@@ -33,7 +33,7 @@ def _run(cloud, precision, mach, alpha, iters, chunk, cfl, snapshot_every):
 
     from . import lskum as L
     t0 = time.perf_counter()
-    with L.Solver.from_cloud(cloud, precision=precision, cfl=cfl) as s:
+    with L.Solver.from_cloud(cloud, precision=precision, cfl=cfl, **options) as s:
         t_create = time.perf_counter() - t0
         s.set_freestream(mach, alpha)
         s.step(2)  # warm-up: builds the iteration graph
@@ -80,19 +80,27 @@ def main():
     ap.add_argument("--mach", type=float, default=0.85)
     ap.add_argument("--alpha", type=float, default=1.0)
     ap.add_argument("--cfl", type=float, default=0.2)
+    ap.add_argument("--option", action="append", default=[], metavar="NAME=VALUE",
+                    help="a solver option for both precisions (lskum_options field), "
+                         "e.g. wall_factor=1 or order=1; repeatable")
     ap.add_argument("--out", default="precision_study.json")
     args = ap.parse_args()
+    options = {}
+    for kv in args.option:
+        name, value = kv.split("=", 1)
+        options[name] = float(value) if "." in value or "e" in value else int(value)
 
     n_c, n_r = Cl.cloud_dims(args.points)
     t0 = time.perf_counter()
     cloud = Cl.naca0012_cloud(n_c, n_r, shuffle=True)
     t_cloud = time.perf_counter() - t0
     out = {"points": cloud.n, "n_c": n_c, "n_r": n_r, "mach": args.mach, "alpha_deg": args.alpha,
-           "iterations": args.iters, "cfl": args.cfl, "cloud_seconds": t_cloud}
+           "iterations": args.iters, "cfl": args.cfl, "options": options,
+           "cloud_seconds": t_cloud}
     r64, W64 = _run(cloud, L.FP64, args.mach, args.alpha, args.iters, args.chunk, args.cfl,
-                    args.snapshot_every)
+                    args.snapshot_every, options)
     rmx, Wmx = _run(cloud, L.MIXED, args.mach, args.alpha, args.iters, args.chunk, args.cfl,
-                    args.snapshot_every)
+                    args.snapshot_every, options)
     scale = np.abs(W64).max(axis=0)
     out["fp64"] = r64
     out["mixed"] = rmx
