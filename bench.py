@@ -195,17 +195,18 @@ def _fp64_peak():
 
 # Per-unit figures of the FP64 flux/update kernel (k_flux), from one ncu
 # capture of a stage launch on the 600,138-point cloud (8,338,298 neighbour
-# entries): 1.1095e9 DFMA, 0.2814e9 DADD and 0.6531e9 DMUL thread
-# instructions (predicated on) = 3.153e9 FP64 flops = 378.2 flops per
-# neighbour entry, and 438.2 MB of DRAM traffic = 730.1 bytes per point.
+# entries): 1.0356e9 DFMA, 0.2712e9 DADD and 0.6062e9 DMUL thread
+# instructions (predicated on) = 2.948e9 FP64 flops = 353.6 flops per
+# neighbour entry (229.4 FP64 instructions), and 438.3 MB of DRAM traffic
+# = 730.3 bytes per point.
 # Units of one launch: neighbour entries (flops) and points (bytes); both
 # scale in proportion with the cloud size. With this instruction mix a
 # saturated FP64 pipe reaches (2 DFMA + DADD + DMUL) / (2 (DFMA + DADD +
 # DMUL)) = 0.771 of the FMA peak (every FP64 instruction takes one issue
 # slot of the pipe).
-FLUX_FP64_FLOPS_PER_NEIGHBOUR = 378.2
-FLUX_FP64_INSTR_PER_NEIGHBOUR = 245.1  # DFMA + DADD + DMUL
-FLUX_DRAM_BYTES_PER_POINT = 730.1
+FLUX_FP64_FLOPS_PER_NEIGHBOUR = 353.6
+FLUX_FP64_INSTR_PER_NEIGHBOUR = 229.4  # DFMA + DADD + DMUL
+FLUX_DRAM_BYTES_PER_POINT = 730.3
 FLUX_FRAC_CEILING = 0.771
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # 1.2586
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 80.55: 128 FP32 lanes per SM
@@ -218,13 +219,13 @@ ALGORITHMIC_BYTES_PER_POINT_ITERATION = 4600.0  # minimal passes, gathers from c
 #          epilogue (state update, q-variables) is per point;
 #   split: the four k_flux_part launches and k_stage_split of one stage.
 #   mixed: 0.8738e9 FFMA + 1.1138e9 FMUL + 0.5614e9 FADD = 3.423e9 FP32 flops
-#          = 410.5 per entry (plus 57 FP64 instructions per point), 277.2 MB
-#          of DRAM traffic = 461.9 bytes per point;
+#          = 410.5 per entry (plus 57 FP64 instructions per point), 280.3 MB
+#          of DRAM traffic = 467.0 bytes per point;
 #   split: 1.5089e9 DFMA + 0.3385e9 DADD + 0.9360e9 DMUL over the five
 #          launches of a stage = 4.292e9 FP64 flops = 514.8 per entry,
 #          1354.5 MB = 2257 bytes per point.
 FLUX_MX_FP32_FLOPS_PER_NEIGHBOUR = 410.5
-FLUX_MX_DRAM_BYTES_PER_POINT = 461.9
+FLUX_MX_DRAM_BYTES_PER_POINT = 467.0
 FLUX_SPLIT_FP64_FLOPS_PER_NEIGHBOUR = 514.8
 FLUX_SPLIT_DRAM_BYTES_PER_POINT = 2257.0
 

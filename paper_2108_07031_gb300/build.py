@@ -23,7 +23,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CUDA_SOURCES = ["lskum_kernels.cu", "lskum_kernels_mixed.cu", "lskum_api.cu", "lskum_noalloc.cu",
                 "mlp_kernels.cu"]
 HOST_SOURCES = ["lskum_setup.cpp"]
-HEADERS = ["lskum_internal.h", "lskum_kernels.cuh", "math_tables.h"]
+HEADERS = ["lskum_internal.h", "lskum_kernels.cuh", "math_tables.h", "device_math.cuh"]
 
 
 def _nvcc() -> str:

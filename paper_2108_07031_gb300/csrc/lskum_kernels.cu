@@ -24,6 +24,7 @@
 
 #include <cmath>
 
+#include "device_math.cuh"
 #include "lskum_internal.h"
 #include "math_tables.h"
 #include "lskum_kernels.cuh"
@@ -50,9 +51,9 @@ __device__ __forceinline__ double bitsd(const int64_t b) { return __longlong_as_
 
 // Primitive state of one modified state q~ in the flux's frame, with the
 // per-state factors the split fluxes share: sqrt(beta), 1/sqrt(pi beta),
-// p + rho e and rho e + p/2 (|u|^2 is frame-invariant, so these are too).
+// h = p + rho e and mhp = -p/2 (|u|^2 is frame-invariant, so these are too).
 struct Prim {
-    double r, u, v, p, sb, cb, h, k;
+    double r, u, v, p, sb, cb, h, mhp;
 };
 
 // exp(x) 2^-HALVE by Tang's table-driven method (math_tables.h): x = k ln2/N
@@ -107,7 +108,7 @@ __device__ __forceinline__ Prim q_to_prim(const double t0, const double t1, cons
     w.p = w.r * inv2b;
     const double rhoe = fma(0.5 * w.r, uu, w.p * gm1_inv);
     w.h = w.p + rhoe;
-    w.k = fma(0.5, w.p, rhoe);
+    w.mhp = -0.5 * w.p;
     return w;
 }
 
@@ -149,12 +150,13 @@ __device__ __forceinline__ void split_flux_a(const Prim& w, const double ua, con
     const int64_t xbits = dbits(S) ^ nmask ^ kSignBit;
     const double A = xbits > 0 ? hc : 1.0 - hc;
     const double Bs = bitsd(dbits(eh * w.cb) ^ nmask);  // sg B
+    // with t = ua A + sg B: G1 = ua G0 + p A, and G4 = h t - (p/2) sg B since
+    // h - p/2 = rho e + p/2 (seven FP64 operations for G instead of ten)
     const double t = fma(ua, A, Bs);
     g[0] = w.r * t;
-    const double ru = w.r * ua;
-    g[1] = fma(fma(ru, ua, w.p), A, ru * Bs);
+    g[1] = fma(ua, g[0], w.p * A);
     g[2] = g[0] * ub;
-    g[3] = fma(w.h * ua, A, w.k * Bs);
+    g[3] = fma(w.h, t, w.mhp * Bs);
 }
 
 // Modified states q~_j and q~_0 of Eq. 28 for one neighbour (half offsets
@@ -184,15 +186,6 @@ __device__ __forceinline__ void prim_to_q(const double rho, const double u, cons
     q.b = 2.0 * beta * u;
     q.c = 2.0 * beta * v;
     q.d = -2.0 * beta;
-}
-
-__device__ __forceinline__ void cons_to_q(const V4& U, const Physics& ph, V4& q, double& rho,
-                                          double& u, double& v, double& p) {
-    rho = U.a;
-    u = U.b / rho;
-    v = U.c / rho;
-    p = ph.gm1 * (U.d - 0.5 * rho * (u * u + v * v));
-    prim_to_q(rho, u, v, p, ph, q);
 }
 
 __device__ __forceinline__ bool physical(double rho, double u, double v, double p) {
@@ -296,7 +289,7 @@ __global__ void __launch_bounds__(BLOCK) k_ls_inner(const DevGeom g, const V8* _
 // kernel and the split-flux ablation: mode 0 stores R; modes 1..4 apply the
 // stage update, the wall condition and the next q; stage 1 also stores dt
 // and U0 and returns R_rho^2 for the residue.
-template <int MODE>
+template <int MODE, bool G14>
 __device__ __forceinline__ double stage_epilogue(const DevGeom& g, const Physics& ph,
                                                  const DevState& st, const int64_t t,
                                                  const int64_t d, const int8_t fl, const bool fixed,
@@ -342,7 +335,7 @@ __device__ __forceinline__ double stage_epilogue(const DevGeom& g, const Physics
         }
         V4 qn;
         double rho, u, v, p;
-        cons_to_q(U, ph, qn, rho, u, v, p);
+        cons_to_q64<G14>(U, ph, qn, rho, u, v, p);
         q_out[t] = qn;
         if (!physical(rho, u, v, p)) atomicOr(st.status, 1);
     }
@@ -430,7 +423,7 @@ __global__ void __launch_bounds__(BLOCK) k_flux(const DevGeom g, const Physics p
                 R[2] = rs * ty + rn * ny;
             }
         }
-        r2 = stage_epilogue<MODE>(g, ph, st, t, d, fl, fixed, R, q_out);
+        r2 = stage_epilogue<MODE, G14>(g, ph, st, t, d, fl, fixed, R, q_out);
     }
     if (MODE == 1) {
         if (g.cshift == 0) {  // one condition: fused block partial sums
@@ -530,7 +523,7 @@ __global__ void __launch_bounds__(BLOCK) k_flux_part(const DevGeom g, const Phys
     }
 }
 
-template <int MODE, int BLOCK>
+template <int MODE, int BLOCK, bool G14>
 __global__ void __launch_bounds__(BLOCK) k_stage_split(const DevGeom g, const Physics ph,
                                                        const DevState st, const V4* __restrict__ Racc,
                                                        V4* __restrict__ q_out) {
@@ -555,7 +548,7 @@ __global__ void __launch_bounds__(BLOCK) k_stage_split(const DevGeom g, const Ph
                 R[2] = rs * ty + rn * nn.y;
             }
         }
-        r2 = stage_epilogue<MODE>(g, ph, st, t, d, fl, fixed, R, q_out);
+        r2 = stage_epilogue<MODE, G14>(g, ph, st, t, d, fl, fixed, R, q_out);
     }
     if (MODE == 1) {
         if (g.cshift == 0) {
@@ -642,7 +635,10 @@ __global__ void k_q_from_U(const DevGeom g, const Physics ph, const V4* __restri
     if ((t >> g.cshift) >= g.n) return;
     V4 qq;
     double rho, uu, vv, p;
-    cons_to_q(U[t], ph, qq, rho, uu, vv, p);
+    if (fabs(ph.gm1_inv - 2.5) < 1e-12)
+        cons_to_q64<true>(U[t], ph, qq, rho, uu, vv, p);
+    else
+        cons_to_q64<false>(U[t], ph, qq, rho, uu, vv, p);
     q[t] = qq;
 }
 
@@ -782,11 +778,11 @@ static void flux_split_dispatch(int mode, const DevGeom& g, const Physics& ph, c
     k_flux_part<2, BLOCK, G14><<<grid, BLOCK, 0, s>>>(g, ph, q_in, dq, Racc);
     k_flux_part<3, BLOCK, G14><<<grid, BLOCK, 0, s>>>(g, ph, q_in, dq, Racc);
     switch (mode) {
-        case 0: k_stage_split<0, BLOCK><<<grid, BLOCK, 0, s>>>(g, ph, st, Racc, q_out); break;
-        case 1: k_stage_split<1, BLOCK><<<grid, BLOCK, 0, s>>>(g, ph, st, Racc, q_out); break;
-        case 2: k_stage_split<2, BLOCK><<<grid, BLOCK, 0, s>>>(g, ph, st, Racc, q_out); break;
-        case 3: k_stage_split<3, BLOCK><<<grid, BLOCK, 0, s>>>(g, ph, st, Racc, q_out); break;
-        default: k_stage_split<4, BLOCK><<<grid, BLOCK, 0, s>>>(g, ph, st, Racc, q_out); break;
+        case 0: k_stage_split<0, BLOCK, G14><<<grid, BLOCK, 0, s>>>(g, ph, st, Racc, q_out); break;
+        case 1: k_stage_split<1, BLOCK, G14><<<grid, BLOCK, 0, s>>>(g, ph, st, Racc, q_out); break;
+        case 2: k_stage_split<2, BLOCK, G14><<<grid, BLOCK, 0, s>>>(g, ph, st, Racc, q_out); break;
+        case 3: k_stage_split<3, BLOCK, G14><<<grid, BLOCK, 0, s>>>(g, ph, st, Racc, q_out); break;
+        default: k_stage_split<4, BLOCK, G14><<<grid, BLOCK, 0, s>>>(g, ph, st, Racc, q_out); break;
     }
 }
 
