@@ -221,12 +221,12 @@ ALGORITHMIC_BYTES_PER_POINT_ITERATION = 4600.0  # minimal passes, gathers from c
 #   mixed: 0.8738e9 FFMA + 1.1138e9 FMUL + 0.5614e9 FADD = 3.423e9 FP32 flops
 #          = 410.5 per entry (plus 57 FP64 instructions per point), 280.3 MB
 #          of DRAM traffic = 467.0 bytes per point;
-#   split: 1.5089e9 DFMA + 0.3385e9 DADD + 0.9360e9 DMUL over the five
-#          launches of a stage = 4.292e9 FP64 flops = 514.8 per entry,
-#          1354.5 MB = 2257 bytes per point.
+#   split: 1.4183e9 DFMA + 0.3283e9 DADD + 0.9057e9 DMUL over the five
+#          launches of a stage = 4.071e9 FP64 flops = 488.2 per entry,
+#          1354.6 MB = 2257 bytes per point.
 FLUX_MX_FP32_FLOPS_PER_NEIGHBOUR = 410.5
 FLUX_MX_DRAM_BYTES_PER_POINT = 467.0
-FLUX_SPLIT_FP64_FLOPS_PER_NEIGHBOUR = 514.8
+FLUX_SPLIT_FP64_FLOPS_PER_NEIGHBOUR = 488.2
 FLUX_SPLIT_DRAM_BYTES_PER_POINT = 2257.0
 
 
