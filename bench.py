@@ -611,7 +611,10 @@ def run_reference(args, rank, world):
         "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "impl": "reference",
+        # the arms share the workload's config; the points this arm actually
+        # iterates (a bounded inner region of that cloud) are named here
         "config": workload_config(args.points, world, mach=args.mach, alpha=args.alpha),
+        "timed_points": n,
         "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": cores,
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
