@@ -489,6 +489,8 @@ def time_variant(args, cloud, precision, n_cond, stream, barrier, dist, what,
     mixed = precision == L.MIXED
     return {"workload": what, "precision": "mixed" if mixed else "fp64",
             "points": cloud.n, "conditions": n_cond, "block_size": {"flux": block[0], "q_derivatives": block[1]},
+            "autotune_space": ({"flux": [128, 256], "q_derivatives": [128, 256]} if autotune
+                               else None),
             "value": value, "unit": "point-condition-iterations/s" if n_cond > 1 else UNIT,
             "ms_per_step": t_max / args.steps, "gpu_launches": int(launches),
             "kernel_ms": {k: {"total_ms": v[0], "launches": v[1]} for k, v in kt.items()},
