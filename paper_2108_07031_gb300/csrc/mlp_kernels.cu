@@ -147,6 +147,63 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(const __nv_bfloat16* __restri
             }
 }
 
+// Narrow output layer, C(m, n) = sum_k X(m, k) W(n, k) + bias(n) for N <=
+// kNarrowMax outputs (the network's 4-wide last layer): one warp per row of
+// X, each lane a 16-byte chunk of eight k per step (a row of 256 is one
+// coalesced 512-byte read), W staged once per block in shared memory, FP32
+// accumulation of the exact BF16 products, a butterfly sum over the lanes.
+// The tiled GEMMs would leave 60 of their 64 (or 124 of 128) columns idle.
+// Requirements (checked by the caller): K a multiple of 8, X rows and W
+// 16-byte aligned, N <= kNarrowMax, N x K <= kNarrowW.
+constexpr int kNarrowMax = 8;
+constexpr int kNarrowW = 4096;  // bf16 elements of W in shared memory (8 KB)
+constexpr int kNarrowRows = 8;  // rows (warps) per block
+
+__global__ void __launch_bounds__(32 * kNarrowRows) k_gemm_narrow(
+    const __nv_bfloat16* __restrict__ X, int64_t sxm, const __nv_bfloat16* __restrict__ W, int M,
+    int N, int K, const float* __restrict__ bias, float* __restrict__ C, int64_t ldc) {
+    __shared__ __align__(16) __nv_bfloat16 Ws[kNarrowW];
+    const int tid = threadIdx.x, lane = tid & 31;
+    for (int e = tid * 8; e < N * K; e += 32 * kNarrowRows * 8)
+        *reinterpret_cast<uint4*>(&Ws[e]) = *reinterpret_cast<const uint4*>(W + e);
+    __syncthreads();
+    const int m = blockIdx.x * kNarrowRows + (tid >> 5);
+    if (m >= M) return;
+    float acc[kNarrowMax];
+#pragma unroll
+    for (int n = 0; n < kNarrowMax; ++n) acc[n] = 0.f;
+    const __nv_bfloat16* x = X + int64_t(m) * sxm;
+    for (int k0 = lane * 8; k0 < K; k0 += 256) {
+        const uint4 xv = *reinterpret_cast<const uint4*>(x + k0);
+        const __nv_bfloat162* xp = reinterpret_cast<const __nv_bfloat162*>(&xv);
+#pragma unroll
+        for (int n = 0; n < kNarrowMax; ++n) {
+            if (n < N) {
+                const uint4 wv = *reinterpret_cast<const uint4*>(&Ws[n * K + k0]);
+                const __nv_bfloat162* wp = reinterpret_cast<const __nv_bfloat162*>(&wv);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float2 xf = __bfloat1622float2(xp[q]);
+                    const float2 wf = __bfloat1622float2(wp[q]);
+                    acc[n] = fmaf(xf.x, wf.x, acc[n]);
+                    acc[n] = fmaf(xf.y, wf.y, acc[n]);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int n = 0; n < kNarrowMax; ++n)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[n] += __shfl_xor_sync(0xffffffffu, acc[n], o);
+    if (lane < N) {
+        float v = acc[0];
+#pragma unroll
+        for (int n = 1; n < kNarrowMax; ++n)
+            if (lane == n) v = acc[n];
+        C[int64_t(m) * ldc + lane] = v + bias[lane];
+    }
+}
+
 // Pipelined GEMM for the aligned, large shapes: 128 x 128 tiles per block of
 // eight warps (each 64 x 32), k in stages of 32 moved global -> shared by
 // cp.async (16-byte chunks, three stages in flight), operand fragments by
@@ -783,6 +840,14 @@ template <int EPI>
 cudaError_t gemm(lskum_mlp* h, const __nv_bfloat16* A, int64_t sam, int64_t sak,
                  const __nv_bfloat16* B, int64_t sbk, int64_t sbn, int M, int N, int K,
                  const float* bias, float* Cf, __nv_bfloat16* Cb, int64_t ldc) {
+    // forward X W^T into few outputs (the last layer): a warp per row
+    if (EPI == kBiasLinear && sak == 1 && sbk == 1 && sbn == K && N <= kNarrowMax &&
+        int64_t(N) * K <= kNarrowW && K % 8 == 0 && sam % 8 == 0 &&
+        !(reinterpret_cast<uintptr_t>(A) & 15) && !(reinterpret_cast<uintptr_t>(B) & 15)) {
+        k_gemm_narrow<<<blocks(M, kNarrowRows), 32 * kNarrowRows, 0, h->stream>>>(A, sam, B, M, N, K,
+                                                                                  bias, Cf, ldc);
+        return cudaGetLastError();
+    }
     if (tc_ok(A, sam, sak, B, sbk, sbn, M, N, K)) {
         const dim3 grid(blocks(N, kTB), blocks(M, kTB), 1);
         const int kchunk = int(blocks(K, kTK)) * kTK;
