@@ -218,14 +218,14 @@ ALGORITHMIC_BYTES_PER_POINT_ITERATION = 4600.0  # minimal passes, gathers from c
 #   mixed: k_flux_mx, FP32 flops (2 FFMA + FADD + FMUL) per entry; its FP64
 #          epilogue (state update, q-variables) is per point;
 #   split: the four k_flux_part launches and k_stage_split of one stage.
-#   mixed: 0.8738e9 FFMA + 1.1138e9 FMUL + 0.5614e9 FADD = 3.423e9 FP32 flops
-#          = 410.5 per entry (plus 57 FP64 instructions per point), 280.3 MB
-#          of DRAM traffic = 467.0 bytes per point;
+#   mixed: 0.7822e9 FFMA + 1.0223e9 FMUL + 0.5091e9 FADD = 3.096e9 FP32 flops
+#          = 371.3 per entry (plus 57 FP64 instructions per point), 277.0 MB
+#          of DRAM traffic = 461.6 bytes per point;
 #   split: 1.4183e9 DFMA + 0.3283e9 DADD + 0.9057e9 DMUL over the five
 #          launches of a stage = 4.071e9 FP64 flops = 488.2 per entry,
 #          1354.6 MB = 2257 bytes per point.
-FLUX_MX_FP32_FLOPS_PER_NEIGHBOUR = 410.5
-FLUX_MX_DRAM_BYTES_PER_POINT = 467.0
+FLUX_MX_FP32_FLOPS_PER_NEIGHBOUR = 371.3
+FLUX_MX_DRAM_BYTES_PER_POINT = 461.6
 FLUX_SPLIT_FP64_FLOPS_PER_NEIGHBOUR = 488.2
 FLUX_SPLIT_DRAM_BYTES_PER_POINT = 2257.0
 

@@ -166,9 +166,9 @@ struct PrimPair {
     float r, u, v, p, sb;       // base state (of q~_0): density, velocity, pressure, sqrt(beta)
     float dr, du, dv, dp, dsb;  // difference state(q~_j) - state(q~_0)
     float isb, isbj;            // 1/sqrt(beta) of the base and of state j
-    // frame-invariant factors both split fluxes of the pair share (base and
-    // difference): p + rho e and rho e + p/2
-    float h, dh, k, dk;
+    // frame-invariant factor both split fluxes of the pair share (base and
+    // difference): h = p + rho e
+    float h, dh;
 };
 
 // e^x - 1: its Taylor polynomial to x^5/120 for |x| <= 1/16 (the remainder is
@@ -236,8 +236,6 @@ __device__ __forceinline__ PrimPair prim_pair(const float4 b, const float4 dq, c
     const float dE = w.dp * gm1_inv + 0.5f * (w.dr * uuj + w.r * duu);
     w.h = w.p + E0;
     w.dh = w.dp + dE;
-    w.k = E0 + 0.5f * w.p;
-    w.dk = dE + 0.5f * w.dp;
     return w;
 }
 
@@ -288,7 +286,7 @@ __device__ __forceinline__ void dsplit_flux_a(const PrimPair& w, const float ua0
                                               float dG[4]) {
     const float r0 = w.r, dr = w.dr, p0 = w.p, dp = w.dp, sb0 = w.sb, dsb = w.dsb;
     const float isb0 = w.isb, isbj = w.isbj;
-    const float uaj = ua0 + dua, ubj = ub0 + dub, sbj = sb0 + dsb;
+    const float sbj = sb0 + dsb;
     const float S0 = ua0 * sb0;
     const float dS = dua * sbj + ua0 * dsb;
     const float Sj = S0 + dS;
@@ -315,22 +313,16 @@ __device__ __forceinline__ void dsplit_flux_a(const PrimPair& w, const float ua0
     const float t0 = ua0 * A0 + sg * B0;
     const float dt = dua * Aj + ua0 * dA + sg * dB;
     const float tj = t0 + dt;
-    // mass: rho t
+    // mass: G0 = rho t
+    const float G00 = r0 * t0;
     dG[0] = dr * tj + r0 * dt;
-    // a-momentum: (p + rho u_a^2) A + sg rho u_a B
-    const float P0 = p0 + r0 * ua0 * ua0;
-    const float dP = dp + dr * uaj * uaj + r0 * dua * (uaj + ua0);
-    const float ru0 = r0 * ua0;
-    const float dru = dr * uaj + r0 * dua;
-    dG[1] = dP * Aj + P0 * dA + sg * (dru * Bj + ru0 * dB);
-    // b-momentum: rho u_b t
-    const float rb0 = r0 * ub0;
-    const float drb = dr * ubj + r0 * dub;
-    dG[2] = drb * tj + rb0 * dt;
-    // energy: (p + rho e) u_a A + sg (rho e + p/2) B
-    const float Q0 = w.h * ua0;
-    const float dQ = w.dh * uaj + w.h * dua;
-    dG[3] = dQ * Aj + Q0 * dA + sg * (w.dk * Bj + w.k * dB);
+    const float G0j = G00 + dG[0];
+    // a-momentum: (p + rho u_a^2) A + sg rho u_a B = u_a G0 + p A
+    dG[1] = dua * G0j + ua0 * dG[0] + (dp * Aj + p0 * dA);
+    // b-momentum: rho u_b t = u_b G0
+    dG[2] = dub * G0j + ub0 * dG[0];
+    // energy: (p + rho e) u_a A + sg (rho e + p/2) B = h t - (p/2) sg B
+    dG[3] = w.dh * tj + w.h * dt - 0.5f * sg * (dp * Bj + p0 * dB);
 }
 
 __device__ __forceinline__ QHL split_hl(const V4& q) {
@@ -365,12 +357,15 @@ __device__ __forceinline__ double block_sum(double x) {
 
 // ------------------------------------------------------- flux residual + RK
 
-// Registers capped at 64 per thread (eight blocks of 128 per SM): the kernel
-// is latency bound, and the extra resident warps gain more than the few
-// spilled words cost (measured: 2.66 against 2.74 ms per launch at 10M
-// points with the 72-register, seven-block cap).
+// Latency bound (long-scoreboard stalls lead): each neighbour entry's stream
+// loads (packed word, FP32 constants) are issued one entry ahead, during the
+// previous entry's flux arithmetic, so only the gathers they index are
+// waited on. Registers capped at 72 per thread (seven blocks of 128 per SM);
+// measured at 10M points: 2.35 ms per launch, against 2.60 without the
+// prefetch at 64 registers (eight blocks) and 2.69 with it at 64 (the
+// prefetched words then spill).
 template <int MODE, int BLOCK, bool G14>
-__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_flux_mx(const DevGeom g, const DevGeom32 g32,
+__global__ void __launch_bounds__(BLOCK, 896 / BLOCK) k_flux_mx(const DevGeom g, const DevGeom32 g32,
                                                    const Physics ph, const DevState st,
                                                    const QHL* __restrict__ q_in,
                                                    const D8f* __restrict__ dq,
@@ -400,14 +395,24 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_flux_mx(const DevGeom g
             const float gm1_inv = float(ph.gm1_inv);
             const bool second = ph.order == 2;
             const int c = g.cnt[d];
+            uint32_t e_next = 0u;
+            float4 fw_next = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (c > 0) {
+                e_next = g.nbr[d];
+                fw_next = g32.fxw[d];
+            }
             for (int k = 0; k < c; ++k) {
-                const int64_t at = int64_t(k) * g.stride + d;
-                const uint32_t e = g.nbr[at];
+                const uint32_t e = e_next;
+                const float4 fw = fw_next;
+                if (k + 1 < c) {  // the next entry's stream, in flight during this one
+                    const int64_t at = int64_t(k + 1) * g.stride + d;
+                    e_next = g.nbr[at];
+                    fw_next = g32.fxw[at];
+                }
                 const uint32_t j = e & kIndexMask;
                 const uint32_t sc = (e >> kIndexBits) & 3u;
                 const uint32_t nc = (e >> (kIndexBits + 2)) & 3u;
                 const int64_t jt = sidx(g, j, cc);
-                const float4 fw = g32.fxw[at];
                 const float4 dqv = qdiff(q_in[jt], qi);
                 float4 base = qiv, dlt = dqv;
                 if (second) {
