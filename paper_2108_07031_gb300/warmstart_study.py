@@ -7,8 +7,10 @@ Cloud: the NACA 0012 cloud of --cloud points (default 128 x 40 = 5,120).
 Training: --train seeded conditions (default 256), M ~ U[0.3, 0.8],
 alpha ~ U[-4, 6] deg, each solved by the batched mixed-precision solver (64
 conditions per launch, CFL 0.8: the converged state does not depend on the
-pseudo-time step) to a 7-order residue drop. Network: the 6-layer, width-256 BF16 tensor-core MLP, Adam with
-a cosine schedule. Evaluation: 32 held-out conditions (another seed), each
+pseudo-time step) to a 7-order residue drop. Network: the 6-layer,
+width-256 BF16 tensor-core MLP, Adam with a cosine schedule; with
+--ensemble K, K networks from different seeds whose predicted states are
+averaged. Evaluation: 32 held-out conditions (another seed), each
 solved from the free stream and from the network's prediction (whose
 far-field points keep the exact free stream: they are boundary data) at the
 configuration's CFL 0.2 (--eval-cfl); reported: iterations until the residue
@@ -41,6 +43,8 @@ def main():
     ap.add_argument("--train", type=int, default=256)
     ap.add_argument("--test", type=int, default=32)
     ap.add_argument("--epochs", type=int, default=240)
+    ap.add_argument("--ensemble", type=int, default=1,
+                    help="networks trained from different seeds; the prediction is their mean state")
     ap.add_argument("--eval-cfl", type=float, default=0.2)
     ap.add_argument("--eval-iters", type=int, default=60_000)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
@@ -77,17 +81,23 @@ def main():
     raw = np.concatenate(S.raw_inputs(cloud, wd, m_tr, a_tr))
     T = np.concatenate([S.targets(W_tr[k], m_tr[k], a_tr[k]) for k in range(args.train)])
     scales = [float(v) for v in args.proj_scales.split(",")]
-    net = S.MLP(capacity=16384, seed=0, proj=S.projection(scales=scales))
     arc = S.wall_arc(cloud) if args.features == "wall" else None
-    if arc is None:
-        feats = net.features(torch.from_numpy(raw).cuda())
-    else:
-        feats = torch.from_numpy(np.concatenate(
-            [S.wall_features(cloud, wd, arc, m_tr[k], a_tr[k], net.proj) for k in range(args.train)])).cuda()
     Td = torch.from_numpy(T).cuda()
+    nets, losses = [], []
     t0 = time.time()
-    losses = S.train(net, feats, Td, epochs=args.epochs, batch=args.batch, lr=2e-3, lr_final=2e-5,
-                     log=log)
+    for e in range(args.ensemble):
+        net = S.MLP(capacity=16384, seed=e, proj=S.projection(scales=scales))
+        if arc is None:
+            feats = net.features(torch.from_numpy(raw).cuda())
+        else:
+            feats = torch.from_numpy(np.concatenate(
+                [S.wall_features(cloud, wd, arc, m_tr[k], a_tr[k], net.proj)
+                 for k in range(args.train)])).cuda()
+        losses_e = S.train(net, feats, Td, epochs=args.epochs, batch=args.batch, lr=2e-3,
+                           lr_final=2e-5, seed=e, log=log)
+        nets.append(net)
+        losses.append(losses_e)
+        del feats
     t_train = time.time() - t0
 
     # held-out: both starts in one batched solve each (32 conditions)
@@ -95,7 +105,9 @@ def main():
     nc = 1 << int(np.ceil(np.log2(n)))
     pred, fallback = [], 0
     for k in range(n):
-        W = S.predict_state(net, cloud, wd, m_te[k], a_te[k], arc=arc)
+        Ws = [S.predict_state(net, cloud, wd, m_te[k], a_te[k], arc=arc) for net in nets]
+        Ws = [w for w in Ws if w is not None]
+        W = np.mean(Ws, axis=0) if Ws else None
         if W is None:
             fallback += 1
             W = np.tile(S.freestream(m_te[k], a_te[k]), (cloud.n, 1))
@@ -140,7 +152,8 @@ def main():
         "features": args.features,
         "epochs": args.epochs,
         "data_seconds": t_data, "train_seconds": t_train,
-        "loss_first": losses[0], "loss_last": losses[-1], "fallbacks": fallback,
+        "ensemble": args.ensemble,
+        "loss_first": losses[0][0], "loss_last": [l[-1] for l in losses], "fallbacks": fallback,
         "iterations_cold": it_cold.tolist(), "iterations_warm": it_warm.tolist(),
         "converged_both": int(both.sum()),
         "saving_mean": float(saving.mean()) if saving.size else None,
