@@ -195,19 +195,19 @@ def _fp64_peak():
 
 # Per-unit figures of the FP64 flux/update kernel (k_flux), from one ncu
 # capture of a stage launch on the 600,138-point cloud (8,338,298 neighbour
-# entries): 1.0356e9 DFMA, 0.2712e9 DADD and 0.6062e9 DMUL thread
+# entries): 1.0688e9 DFMA, 0.2379e9 DADD and 0.5728e9 DMUL thread
 # instructions (predicated on) = 2.948e9 FP64 flops = 353.6 flops per
-# neighbour entry (229.4 FP64 instructions), and 438.3 MB of DRAM traffic
-# = 730.3 bytes per point.
+# neighbour entry (225.4 FP64 instructions), and 438.0 MB of DRAM traffic
+# = 729.8 bytes per point.
 # Units of one launch: neighbour entries (flops) and points (bytes); both
 # scale in proportion with the cloud size. With this instruction mix a
 # saturated FP64 pipe reaches (2 DFMA + DADD + DMUL) / (2 (DFMA + DADD +
-# DMUL)) = 0.771 of the FMA peak (every FP64 instruction takes one issue
+# DMUL)) = 0.784 of the FMA peak (every FP64 instruction takes one issue
 # slot of the pipe).
 FLUX_FP64_FLOPS_PER_NEIGHBOUR = 353.6
-FLUX_FP64_INSTR_PER_NEIGHBOUR = 229.4  # DFMA + DADD + DMUL
-FLUX_DRAM_BYTES_PER_POINT = 730.3
-FLUX_FRAC_CEILING = 0.771
+FLUX_FP64_INSTR_PER_NEIGHBOUR = 225.4  # DFMA + DADD + DMUL
+FLUX_DRAM_BYTES_PER_POINT = 729.8
+FLUX_FRAC_CEILING = 0.784
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # 1.2586
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 80.55: 128 FP32 lanes per SM
 ALGORITHMIC_BYTES_PER_POINT_ITERATION = 4600.0  # minimal passes, gathers from cache
@@ -221,9 +221,9 @@ ALGORITHMIC_BYTES_PER_POINT_ITERATION = 4600.0  # minimal passes, gathers from c
 #   mixed: 0.7822e9 FFMA + 1.0223e9 FMUL + 0.5091e9 FADD = 3.096e9 FP32 flops
 #          = 371.3 per entry (plus 57 FP64 instructions per point), 277.0 MB
 #          of DRAM traffic = 461.6 bytes per point;
-#   split: 1.4183e9 DFMA + 0.3283e9 DADD + 0.9057e9 DMUL over the five
+#   split: 1.4516e9 DFMA + 0.2950e9 DADD + 0.8724e9 DMUL over the five
 #          launches of a stage = 4.071e9 FP64 flops = 488.2 per entry,
-#          1354.6 MB = 2257 bytes per point.
+#          1353.9 MB = 2256 bytes per point.
 FLUX_MX_FP32_FLOPS_PER_NEIGHBOUR = 371.3
 FLUX_MX_DRAM_BYTES_PER_POINT = 461.6
 FLUX_SPLIT_FP64_FLOPS_PER_NEIGHBOUR = 488.2

@@ -130,8 +130,15 @@ __device__ __forceinline__ int erfcx_piece(const int64_t abits) {
 //        (p + rho e) ua A + sg (rho e + p/2) B).
 // erfc(|S|)/2 = exp(-S^2)/2 erfcx(|S|) from the erfcx pieces for every |S| <= 6
 // (one path for all lanes), sharing exp(-S^2)/2 with B; the library erfc beyond.
-__device__ __forceinline__ void split_flux_a(const Prim& w, const double ua, const double ub,
-                                             const int64_t nmask, double g[4]) {
+// With t = ua A + sg B the four components are G0 = rho t, G1 = ua G0 + p A,
+// G2 = ub G0 and G3 = h t - (p/2) sg B (h - p/2 = rho e + p/2); split_ab
+// returns t, A and sg B of one state, split_flux_diff the four differences
+// between two states.
+struct SplitAB {
+    double t, A, Bs;
+};
+
+__device__ __forceinline__ SplitAB split_ab(const Prim& w, const double ua, const int64_t nmask) {
     const double S = ua * w.sb;
     const double eh = exp_tab<1>(-(S * S));  // exp(-S^2) / 2
     const int64_t abits = dbits(S) & kAbsMask;
@@ -150,13 +157,23 @@ __device__ __forceinline__ void split_flux_a(const Prim& w, const double ua, con
     const int64_t xbits = dbits(S) ^ nmask ^ kSignBit;
     const double A = xbits > 0 ? hc : 1.0 - hc;
     const double Bs = bitsd(dbits(eh * w.cb) ^ nmask);  // sg B
-    // with t = ua A + sg B: G1 = ua G0 + p A, and G4 = h t - (p/2) sg B since
-    // h - p/2 = rho e + p/2 (seven FP64 operations for G instead of ten)
-    const double t = fma(ua, A, Bs);
-    g[0] = w.r * t;
-    g[1] = fma(ua, g[0], w.p * A);
-    g[2] = g[0] * ub;
-    g[3] = fma(w.h, t, w.mhp * Bs);
+    return SplitAB{fma(ua, A, Bs), A, Bs};
+}
+
+// G(state j) - G(state 0) along the frame's first axis (velocities uaj, ubj
+// and ua0, ub0): each difference takes state 0's value, rounded once, into
+// the FMA chain of state j's, so the four cost 13 FP64 operations where two
+// flux evaluations and four subtractions took 16.
+__device__ __forceinline__ void split_flux_diff(const Prim& wj, const Prim& w0, const double uaj,
+                                                const double ubj, const double ua0, const double ub0,
+                                                const SplitAB& aj, const SplitAB& a0, double d[4]) {
+    const double g0j = wj.r * aj.t, g00 = w0.r * a0.t;
+    d[0] = g0j - g00;
+    const double g10 = fma(ua0, g00, w0.p * a0.A);
+    d[1] = fma(uaj, g0j, fma(wj.p, aj.A, -g10));
+    d[2] = fma(g0j, ubj, -(g00 * ub0));
+    const double g30 = fma(w0.h, a0.t, w0.mhp * a0.Bs);
+    d[3] = fma(wj.h, aj.t, fma(wj.mhp, aj.Bs, -g30));
 }
 
 // Modified states q~_j and q~_0 of Eq. 28 for one neighbour (half offsets
@@ -395,26 +412,26 @@ __global__ void __launch_bounds__(BLOCK) k_flux(const DevGeom g, const Physics p
                 }
                 if (sc) {
                     const int64_t nmask = sc == 1u ? 0 : kSignBit;
-                    double gj[4], g0[4];
-                    split_flux_a(wj, wj.u, wj.v, nmask, gj);
-                    split_flux_a(w0, w0.u, w0.v, nmask, g0);
+                    double dg[4];
+                    split_flux_diff(wj, w0, wj.u, wj.v, w0.u, w0.v, split_ab(wj, wj.u, nmask),
+                                    split_ab(w0, w0.u, nmask), dg);
                     const double w = g.ws[at];
-                    R[0] += w * (gj[0] - g0[0]);
-                    R[1] += w * (gj[1] - g0[1]);
-                    R[2] += w * (gj[2] - g0[2]);
-                    R[3] += w * (gj[3] - g0[3]);
+                    R[0] = fma(w, dg[0], R[0]);
+                    R[1] = fma(w, dg[1], R[1]);
+                    R[2] = fma(w, dg[2], R[2]);
+                    R[3] = fma(w, dg[3], R[3]);
                 }
                 if (nc) {
                     const int64_t nmask = nc == 1u ? 0 : kSignBit;
-                    double gj[4], g0[4];
+                    double dg[4];
                     // along n: "a" = n-velocity, "b" = s-velocity
-                    split_flux_a(wj, wj.v, wj.u, nmask, gj);
-                    split_flux_a(w0, w0.v, w0.u, nmask, g0);
+                    split_flux_diff(wj, w0, wj.v, wj.u, w0.v, w0.u, split_ab(wj, wj.v, nmask),
+                                    split_ab(w0, w0.v, nmask), dg);
                     const double w = g.wn[at];
-                    R[0] += w * (gj[0] - g0[0]);
-                    R[1] += w * (gj[2] - g0[2]);  // s-momentum
-                    R[2] += w * (gj[1] - g0[1]);  // n-momentum
-                    R[3] += w * (gj[3] - g0[3]);
+                    R[0] = fma(w, dg[0], R[0]);
+                    R[1] = fma(w, dg[2], R[1]);  // s-momentum
+                    R[2] = fma(w, dg[1], R[2]);  // n-momentum
+                    R[3] = fma(w, dg[3], R[3]);
                 }
             }
             if (local) {  // momentum back to the global frame
@@ -491,23 +508,23 @@ __global__ void __launch_bounds__(BLOCK) k_flux_part(const DevGeom g, const Phys
                 wj.u = sj; wj.v = nj;
                 w0.u = s0; w0.v = n0;
             }
-            double gj[4], g0[4];
+            double dg[4];
             if (PART < 2) {
-                split_flux_a(wj, wj.u, wj.v, nmask, gj);
-                split_flux_a(w0, w0.u, w0.v, nmask, g0);
+                split_flux_diff(wj, w0, wj.u, wj.v, w0.u, w0.v, split_ab(wj, wj.u, nmask),
+                                split_ab(w0, w0.u, nmask), dg);
                 const double w = g.ws[at];
-                R[0] += w * (gj[0] - g0[0]);
-                R[1] += w * (gj[1] - g0[1]);
-                R[2] += w * (gj[2] - g0[2]);
-                R[3] += w * (gj[3] - g0[3]);
+                R[0] = fma(w, dg[0], R[0]);
+                R[1] = fma(w, dg[1], R[1]);
+                R[2] = fma(w, dg[2], R[2]);
+                R[3] = fma(w, dg[3], R[3]);
             } else {
-                split_flux_a(wj, wj.v, wj.u, nmask, gj);
-                split_flux_a(w0, w0.v, w0.u, nmask, g0);
+                split_flux_diff(wj, w0, wj.v, wj.u, w0.v, w0.u, split_ab(wj, wj.v, nmask),
+                                split_ab(w0, w0.v, nmask), dg);
                 const double w = g.wn[at];
-                R[0] += w * (gj[0] - g0[0]);
-                R[1] += w * (gj[2] - g0[2]);
-                R[2] += w * (gj[1] - g0[1]);
-                R[3] += w * (gj[3] - g0[3]);
+                R[0] = fma(w, dg[0], R[0]);
+                R[1] = fma(w, dg[2], R[1]);
+                R[2] = fma(w, dg[1], R[2]);
+                R[3] = fma(w, dg[3], R[3]);
             }
         }
     }
