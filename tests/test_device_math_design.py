@@ -2,10 +2,12 @@
 the table-driven exponential (Tang's reduction with the 2^(j/256) table and
 a degree-4 polynomial), erfc(a)/2 = exp(-a^2)/2 erfcx(a) from the erfcx
 pieces, 1/beta from (1/sqrt(beta))^2 with one Newton step, and the
-table-driven logarithm of the mixed path's FP64 epilogue, all evaluated
-as the kernel does -- every fused multiply-add rounded once, emulated in
-200-bit arithmetic -- against mpmath at 50 digits, with the table values
-read from math_tables.h. CPU only."""
+table-driven logarithm of the stage epilogues, all evaluated as the kernel
+does -- every fused multiply-add rounded once, emulated in 200-bit
+arithmetic -- against mpmath at 50 digits, with the table values read from
+math_tables.h; and the rewritten forms in which the kernels assemble the
+split fluxes, their differences and the q-variables from U, against the
+oracle's direct evaluation. CPU only."""
 
 import math
 import os
@@ -163,3 +165,107 @@ def test_table_log(tables):
         if abs(float(ref)) > 0.1:
             worst_rel = max(worst_rel, err / _ulp(abs(float(ref))))
     assert worst_abs <= 0.5 and worst_rel <= 2.0, (worst_abs, worst_rel)
+
+
+# ---------------------------------------------------------------- algebra
+# The kernels assemble the kinetic split fluxes and the q-variables in
+# rewritten forms. These tests evaluate those forms in float64 with the
+# library's erfc/exp/log and compare them with the oracle's direct
+# evaluation of the same quantities, so a wrong identity (a dropped term, a
+# wrong sign) fails here, on the CPU.
+
+def _states(n, seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    rho = rng.uniform(0.3, 3.0, n)
+    u = rng.uniform(-2.0, 2.0, n)
+    v = rng.uniform(-2.0, 2.0, n)
+    p = rng.uniform(0.2, 3.0, n)
+    return np.stack([rho, u, v, p], axis=1)
+
+
+def _split_ab(W, ua, sg, gamma=1.4):
+    """t = ua A + sg B, A = erfc(-sg S)/2, sg B with B = exp(-S^2)/(2 sqrt(pi beta))."""
+    rho, p = W[:, 0], W[:, 3]
+    beta = rho / (2.0 * p)
+    S = ua * np.sqrt(beta)
+    A = np.array([0.5 * math.erfc(-sg * s) for s in S])
+    B = np.exp(-S * S) / (2.0 * np.sqrt(math.pi * beta))
+    return ua * A + sg * B, A, sg * B
+
+
+def _device_split_flux(W, direction, sg, gamma=1.4):
+    """G0 = rho t, G_a = ua G0 + p A, G_b = ub G0, G3 = h t - (p/2) sg B,
+    the forms of the FP64 flux kernel; returned in the global component order."""
+    rho, u, v, p = W.T
+    ua, ub = (u, v) if direction == 0 else (v, u)
+    t, A, Bs = _split_ab(W, ua, sg, gamma)
+    h = p + p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v)
+    G0 = rho * t
+    Ga = ua * G0 + p * A
+    Gb = ub * G0
+    G3 = h * t - 0.5 * p * Bs
+    mom = (Ga, Gb) if direction == 0 else (Gb, Ga)
+    return np.stack([G0, mom[0], mom[1], G3], axis=1)
+
+
+@pytest.mark.parametrize("direction", [0, 1])
+@pytest.mark.parametrize("sg", [1, -1])
+def test_split_flux_assembly_matches_the_oracle(direction, sg):
+    from oracle import oracle as O
+    W = _states(400, 11 + direction + (sg > 0))
+    ref = O.split_flux(W, direction, sg)
+    got = _device_split_flux(W, direction, sg)
+    scale = np.abs(ref).max(axis=0)
+    assert np.all(np.abs(got - ref).max(axis=0) <= 1e-13 * scale)
+
+
+@pytest.mark.parametrize("direction", [0, 1])
+def test_split_flux_differences_in_one_chain(direction):
+    """The kernel's differences G(j) - G(0) (state 0's component rounded once
+    into state j's FMA chain) against the oracle's two fluxes subtracted, for
+    nearby pairs, within the rounding of the fluxes themselves."""
+    from oracle import oracle as O
+    W0 = _states(300, 29 + direction)
+    rng = np.random.Generator(np.random.PCG64(31 + direction))
+    Wj = W0 * (1.0 + 1e-3 * rng.standard_normal(W0.shape))
+    for sg in (1, -1):
+        rho0, u0, v0, p0 = W0.T
+        rhoj, uj, vj, pj = Wj.T
+        ua0, ub0 = (u0, v0) if direction == 0 else (v0, u0)
+        uaj, ubj = (uj, vj) if direction == 0 else (vj, uj)
+        t0, A0, B0 = _split_ab(W0, ua0, sg)
+        tj, Aj, Bj = _split_ab(Wj, uaj, sg)
+        h0 = p0 / 0.4 + p0 + 0.5 * rho0 * (u0 * u0 + v0 * v0)
+        hj = pj / 0.4 + pj + 0.5 * rhoj * (uj * uj + vj * vj)
+        g0j, g00 = rhoj * tj, rho0 * t0
+        d0 = g0j - g00
+        d1 = uaj * g0j + (pj * Aj - (ua0 * g00 + p0 * A0))
+        d2 = g0j * ubj - g00 * ub0
+        d3 = hj * tj + (-0.5 * pj * Bj - (h0 * t0 - 0.5 * p0 * B0))
+        da, db = (d1, d2) if direction == 0 else (d2, d1)
+        got = np.stack([d0, da, db, d3], axis=1)
+        ref = O.split_flux(Wj, direction, sg) - O.split_flux(W0, direction, sg)
+        scale = np.abs(O.split_flux(W0, direction, sg)).max(axis=0)
+        assert np.all(np.abs(got - ref).max(axis=0) <= 1e-13 * scale)
+
+
+def test_q_variables_from_conserved_state():
+    """q from U as the stage epilogues form it: rho p without a division, one
+    reciprocal of rho^2 p for 1/rho and 1/p, and for gamma = 1.4
+    q1 = ln(rho^2 beta^5)/2 - beta |u|^2 -- against Eq. 26 of the oracle
+    applied to the primitive state."""
+    from oracle import oracle as O
+    W = _states(500, 5)
+    U = O.prim_to_cons(W)
+    gm1 = 0.4
+    rho = U[:, 0]
+    m2 = U[:, 1] ** 2 + U[:, 2] ** 2
+    rp = gm1 * (U[:, 3] * rho - 0.5 * m2)
+    rr = 1.0 / (rho * rp)
+    ip = rho * rho * rr
+    beta = 0.5 * rho * ip
+    q = np.stack([0.5 * np.log(rho * rho * beta ** 5) - 0.5 * m2 * (rho * rr),
+                  U[:, 1] * ip, U[:, 2] * ip, -rho * ip], axis=1)
+    ref = O.prim_to_q(O.cons_to_prim(U))
+    scale = np.abs(ref).max(axis=0)
+    assert np.all(np.abs(q - ref).max(axis=0) <= 1e-13 * scale)
