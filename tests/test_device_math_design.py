@@ -269,3 +269,94 @@ def test_q_variables_from_conserved_state():
     ref = O.prim_to_q(O.cons_to_prim(U))
     scale = np.abs(ref).max(axis=0)
     assert np.all(np.abs(q - ref).max(axis=0) <= 1e-13 * scale)
+
+
+def _mixed_dsplit(b, dq, direction, sg, gm1_inv=2.5):
+    """The mixed path's difference-form split flux, G(q~_0 + dq~) - G(q~_0),
+    as its kernel assembles it (base state and difference from the
+    q-variables, expm1/log1p of the small arguments, the erfc midpoint
+    series), evaluated here in float64 rows."""
+    bx, by, bz, bw = b.T
+    dx_, dy_, dz_, dw_ = dq.T
+    beta, dbeta, qj4 = -0.5 * bw, -0.5 * dw_, bw + dw_
+    inv2b = -1.0 / bw
+    u, v = by * inv2b, bz * inv2b
+    rq = 1.0 / (bw * qj4)
+    du = (by * dw_ - dy_ * bw) * rq
+    dv = (bz * dw_ - dz_ * bw) * rq
+    uj, vj = u + du, v + dv
+    uu0, uuj = u * u + v * v, uj * uj + vj * vj
+    duu = du * (uj + u) + dv * (vj + v)
+    isb = 1.0 / np.sqrt(beta)
+    sb = beta * isb
+    betaj = beta + dbeta
+    isbj = 1.0 / np.sqrt(betaj)
+    dsb = dbeta / (betaj * isbj + sb)
+    i2 = isb * isb
+    r = np.exp(bx + beta * uu0) * (i2 * i2 * isb)
+    dlnr = dx_ - np.log1p(dbeta * (2.0 * inv2b)) * gm1_inv + (dbeta * uuj + beta * duu)
+    dr = r * np.expm1(dlnr)
+    p = r * inv2b
+    dp = (dr * beta - r * dbeta) * (inv2b * (isbj * isbj))
+    E0 = p * gm1_inv + 0.5 * r * uu0
+    dE = dp * gm1_inv + 0.5 * (dr * uuj + r * duu)
+    h, dh = p + E0, dp + dE
+    ua0, ub0, dua, dub = (u, v, du, dv) if direction == 0 else (v, u, dv, du)
+    sbj = sb + dsb
+    S0 = ua0 * sb
+    dS = dua * sbj + ua0 * dsb
+    Sj = S0 + dS
+    e0 = np.exp(-S0 * S0)
+    de = e0 * np.expm1(-dS * (Sj + S0))
+    x0, dx = -sg * S0, -sg * dS
+    A0 = np.array([0.5 * math.erfc(x) for x in x0])
+
+    def central(m, hh):  # erfc(m - h) - erfc(m + h), Hermite midpoint series
+        m2, h2 = m * m, hh * hh
+        H2 = 4 * m2 - 2
+        H4 = (16 * m2 - 48) * m2 + 12
+        H6 = ((64 * m2 - 480) * m2 + 720) * m2 - 120
+        H8 = (((256 * m2 - 3584) * m2 + 13440) * m2 - 13440) * m2 + 1680
+        tail = H4 / 120 + np.where(np.abs(hh) > 1 / 64, h2 * (H6 / 5040 + h2 * H8 / 362880), 0.0)
+        return 4 / math.sqrt(math.pi) * np.exp(-m2) * hh * (1 + h2 * (H2 / 6 + h2 * tail))
+
+    small = np.abs(dx) <= 0.25
+    dA = np.where(small, -0.5 * central(x0 + 0.5 * dx, 0.5 * dx),
+                  np.array([0.5 * (math.erfc(a + d) - math.erfc(a)) for a, d in zip(x0, dx)]))
+    Aj = A0 + dA
+    c = 0.5 / math.sqrt(math.pi)
+    B0 = c * e0 * isb
+    dB = c * (de * isbj - e0 * dsb * isbj * isb)
+    Bj = B0 + dB
+    t0 = ua0 * A0 + sg * B0
+    dt = dua * Aj + ua0 * dA + sg * dB
+    tj = t0 + dt
+    G00 = r * t0
+    dG0 = dr * tj + r * dt
+    G0j = G00 + dG0
+    dGa = dua * G0j + ua0 * dG0 + (dp * Aj + p * dA)
+    dGb = dub * G0j + ub0 * dG0
+    dG3 = dh * tj + h * dt - 0.5 * sg * (dp * Bj + p * dB)
+    mom = (dGa, dGb) if direction == 0 else (dGb, dGa)
+    return np.stack([dG0, mom[0], mom[1], dG3], axis=1)
+
+
+@pytest.mark.parametrize("direction", [0, 1])
+def test_mixed_difference_form_matches_the_oracle(direction):
+    """The mixed kernel's difference-form split flux (base + difference of
+    the modified states, product rule, expm1/log1p, erfc midpoint series) in
+    float64 against the oracle's two fluxes subtracted: the forms are exact
+    up to rounding and the series' truncation, far below the FP32 the kernel
+    evaluates them in."""
+    from oracle import oracle as O
+    W0 = _states(400, 41 + direction)
+    b = O.prim_to_q(W0)
+    rng = np.random.Generator(np.random.PCG64(43 + direction))
+    dq = 1e-3 * np.abs(b) * rng.standard_normal(b.shape)
+    Wj = O.q_to_prim(b + dq)
+    for sg in (1, -1):
+        got = _mixed_dsplit(b, dq, direction, sg)
+        ref = O.split_flux(Wj, direction, sg) - O.split_flux(W0, direction, sg)
+        scale = np.abs(O.split_flux(W0, direction, sg)).max(axis=0)
+        assert np.all(np.abs(got - ref).max(axis=0) <= 1e-12 * scale), \
+            (np.abs(got - ref).max(axis=0) / scale)
