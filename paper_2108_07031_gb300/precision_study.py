@@ -66,6 +66,18 @@ def _run(cloud, precision, mach, alpha, iters, chunk, cfl, snapshot_every, optio
     return out, snap["W"]
 
 
+def parse_options(items) -> dict:
+    """NAME=VALUE strings into solver option keywords: a value with a decimal
+    point or an exponent is a float, anything else an int."""
+    options = {}
+    for kv in items:
+        name, sep, value = kv.partition("=")
+        if not sep or not name:
+            raise ValueError(f"expected NAME=VALUE, got {kv!r}")
+        options[name] = float(value) if any(ch in value for ch in ".eE") else int(value)
+    return options
+
+
 def main():
     from . import cloud as Cl
     from . import lskum as L
@@ -85,10 +97,7 @@ def main():
                          "e.g. wall_factor=1 or order=1; repeatable")
     ap.add_argument("--out", default="precision_study.json")
     args = ap.parse_args()
-    options = {}
-    for kv in args.option:
-        name, value = kv.split("=", 1)
-        options[name] = float(value) if "." in value or "e" in value else int(value)
+    options = parse_options(args.option)
 
     n_c, n_r = Cl.cloud_dims(args.points)
     t0 = time.perf_counter()
